@@ -1,0 +1,189 @@
+/*
+ * ORACLE -- test infrastructure only.
+ *
+ * Plain, slow, obviously correct CPU implementations of what the load-balanced
+ * SpMV path computes, in FP64 where floating point is involved.  Only the test
+ * suite, the smoke check and the benchmark's CPU-baseline leg use this file;
+ * the product path never links or calls it, and it shares no code, header,
+ * table or helper with the CUDA library.
+ *
+ * Notation (Sec. 3.1, Listing 1): a tile is a CSR row, an atom is a nonzero;
+ * rp[R+1] are the row offsets, ci[N] the column indices, v[N] the values.
+ * The atoms of tile t are [rp[t], rp[t+1]) (Listing 2, atoms()).
+ *
+ * Every function states the passage it follows.  Where the paper is silent the
+ * reading used is stated at the function (tie-break in the merge, summation
+ * order, empty rows).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/*
+ * y = A x by the definition of SpMV (Sec. 1; Listing 3 body): for every row i,
+ * y[i] = sum over k in [rp[i], rp[i+1]) of v[k] * x[ci[k]], accumulated in
+ * FP64 in atom order.  Also returns the error scale b[i] = sum |v[k] x[ci[k]]|
+ * used by the acceptance bound |y32 - y64| <= tol * b.  Empty rows give 0.
+ */
+void or_spmv(int32_t R, const int32_t* rp, const int32_t* ci, const float* v, const float* x, double* y,
+             double* b) {
+  for (int32_t i = 0; i < R; ++i) {
+    double s = 0.0, a = 0.0;
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+      double p = (double)v[k] * (double)x[ci[k]];
+      s += p;
+      a += fabs(p);
+    }
+    y[i] = s;
+    if (b) b[i] = a;
+  }
+}
+
+/*
+ * Same as or_spmv for a subset of rows (sampled parity at full size).
+ */
+void or_spmv_rows(int64_t nsel, const int64_t* rows, const int32_t* rp, const int32_t* ci, const float* v,
+                  const float* x, double* y, double* b) {
+  for (int64_t q = 0; q < nsel; ++q) {
+    int64_t i = rows[q];
+    double s = 0.0, a = 0.0;
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+      double p = (double)v[k] * (double)x[ci[k]];
+      s += p;
+      a += fabs(p);
+    }
+    y[q] = s;
+    if (b) b[q] = a;
+  }
+}
+
+/*
+ * Merge-path split (Sec. 5.2.1; Merrill & Garland's merge-based SpMV, cited
+ * there).  The work list is the merge of list A (row-end markers
+ * A[r] = rp[r+1], r < R) with list B (atom indices B[k] = k, k < N).
+ * Reading of the tie, which the paper leaves open: A[r] precedes B[k] exactly
+ * when A[r] <= k, i.e. a row ends before the atom with the same index starts.
+ *
+ * The split of diagonal d (0 <= d <= R+N) is the pair (i, j), i + j = d, that
+ * puts the first i markers and the first j atoms before the rest.  It is the
+ * smallest i in [max(0, d-N), min(d, R)] for which either i is that upper
+ * limit or atom j-1 = d-i-1 precedes marker A[i] (rp[i+1] > d-i-1); the test
+ * is monotone in i, so a bisection along the diagonal finds it.
+ * Returns i; j = d - i.
+ */
+int32_t or_merge_split(int64_t d, int32_t R, int32_t N, const int32_t* rp) {
+  int64_t lo = d - (int64_t)N;
+  if (lo < 0) lo = 0;
+  int64_t hi = d < (int64_t)R ? d : (int64_t)R;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) / 2;
+    if ((int64_t)rp[mid + 1] > d - mid - 1) hi = mid;
+    else lo = mid + 1;
+  }
+  return (int32_t)lo;
+}
+
+/* Splits for a list of diagonals: out[2q] = i, out[2q+1] = j. */
+void or_merge_splits(int64_t nd, const int64_t* diag, int32_t R, int32_t N, const int32_t* rp, int32_t* out) {
+  for (int64_t q = 0; q < nd; ++q) {
+    int32_t i = or_merge_split(diag[q], R, N, rp);
+    out[2 * q] = i;
+    out[2 * q + 1] = (int32_t)(diag[q] - i);
+  }
+}
+
+/*
+ * The full merged work list, written out item by item (Sec. 5.2.1): kind[q] is
+ * 0 for a row-end marker and 1 for an atom, idx[q] the row or atom index.
+ * Same tie reading as or_merge_split.  Length R + N.
+ */
+void or_merge_sequence(int32_t R, int32_t N, const int32_t* rp, int8_t* kind, int32_t* idx) {
+  int32_t i = 0, j = 0;
+  int64_t q = 0;
+  while (i < R || j < N) {
+    if (i < R && (j >= N || rp[i + 1] <= j)) {
+      kind[q] = 0;
+      idx[q] = i++;
+    } else {
+      kind[q] = 1;
+      idx[q] = j++;
+    }
+    ++q;
+  }
+}
+
+/*
+ * Tile of every atom (the mapping a schedule's get_tile returns, Sec. 5.2.3):
+ * row_of[k] = the row r with rp[r] <= k < rp[r+1], by walking the rows.
+ */
+void or_row_of_atom(int32_t R, const int32_t* rp, int32_t* row_of) {
+  for (int32_t r = 0; r < R; ++r)
+    for (int32_t k = rp[r]; k < rp[r + 1]; ++k) row_of[k] = r;
+}
+
+/*
+ * get_tile(a) of the group-mapped schedule (Sec. 5.2.3): given the exclusive
+ * prefix sum prefix[0..n] of the atoms-per-tile of a group's tiles, the tile
+ * of flattened atom a is the largest t < n with prefix[t] <= a (empty tiles,
+ * whose prefix equals the next one's, are skipped).  Linear scan.
+ */
+int32_t or_get_tile(const int32_t* prefix, int32_t n, int32_t a) {
+  int32_t t = -1;
+  for (int32_t q = 0; q < n; ++q)
+    if (prefix[q] <= a) t = q;
+  return t;
+}
+
+/*
+ * CSR -> CSC by a stable counting sort over the atoms in CSR order
+ * (the transpose the differentiable form needs for dx = A^T dy):
+ * cnt[c] = number of atoms in column c; cp = exclusive prefix of cnt;
+ * atoms are then placed in increasing k, so rows ascend within each column.
+ * perm[p] = source atom k of CSC slot p, riT[p] = row of that atom.
+ */
+void or_transpose(int32_t R, int32_t C, const int32_t* rp, const int32_t* ci, int32_t* cp, int32_t* riT,
+                  int32_t* perm) {
+  int32_t N = rp[R];
+  for (int32_t c = 0; c <= C; ++c) cp[c] = 0;
+  for (int32_t k = 0; k < N; ++k) cp[ci[k] + 1] += 1;
+  for (int32_t c = 0; c < C; ++c) cp[c + 1] += cp[c];
+  int32_t* cur = (int32_t*)malloc(sizeof(int32_t) * (size_t)(C > 0 ? C : 1));
+  for (int32_t c = 0; c < C; ++c) cur[c] = cp[c];
+  for (int32_t r = 0; r < R; ++r) {
+    for (int32_t k = rp[r]; k < rp[r + 1]; ++k) {
+      int32_t p = cur[ci[k]]++;
+      perm[p] = k;
+      riT[p] = r;
+    }
+  }
+  free(cur);
+}
+
+/*
+ * Gradients of y = A x for the loss L = sum_i dy[i] y[i]:
+ *   dx[c]    = sum over atoms k with ci[k] = c of v[k] dy[row(k)]   (A^T dy)
+ *   dvals[k] = dy[row(k)] x[ci[k]]
+ * dx is accumulated in FP64 by scattering over the CSR atoms in k order, with
+ * bound bx[c] = sum |v[k] dy[row(k)]|.  dvals is one product of two FP32
+ * numbers; the FP64 product is exact, so rounding it to FP32 gives the
+ * correctly rounded FP32 product.
+ */
+void or_grad(int32_t R, int32_t C, const int32_t* rp, const int32_t* ci, const float* v, const float* x,
+             const float* dy, double* dx, double* bx, float* dvals) {
+  if (dx) {
+    for (int32_t c = 0; c < C; ++c) dx[c] = 0.0;
+    if (bx)
+      for (int32_t c = 0; c < C; ++c) bx[c] = 0.0;
+  }
+  for (int32_t r = 0; r < R; ++r) {
+    for (int32_t k = rp[r]; k < rp[r + 1]; ++k) {
+      if (dx) {
+        double p = (double)v[k] * (double)dy[r];
+        dx[ci[k]] += p;
+        if (bx) bx[ci[k]] += fabs(p);
+      }
+      if (dvals) dvals[k] = (float)((double)dy[r] * (double)x[ci[k]]);
+    }
+  }
+}
