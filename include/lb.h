@@ -1,0 +1,247 @@
+/*
+ * lb.h -- C ABI of the load-balanced sparse matrix-vector library for GB300 (sm_103a).
+ *
+ * Vocabulary (Osama, Porumbescu, Owens, "A Programming Model for GPU Load
+ * Balancing", PPoPP'23, Sec. 3.1 and Listing 1): a work TILE is a row of a CSR
+ * matrix, a work ATOM is one of its nonzeros, the TILE SET is the matrix.  The
+ * tile set is given by `tile_offsets` (CSR row offsets, int32, num_tiles + 1
+ * entries, tile_offsets[0] = 0, nondecreasing, tile_offsets[num_tiles] =
+ * num_atoms); the atoms of tile t are [tile_offsets[t], tile_offsets[t+1]).
+ *
+ * Schedules (Sec. 4.2 and 5.2): thread-mapped (one tile per thread, Listing 2),
+ * warp-/block-mapped and group-mapped (a group takes a chunk of tiles,
+ * prefix-sums their atom counts in shared memory and walks the flattened atoms,
+ * finding each atom's tile with get_tile, Sec. 5.2.2-5.2.3), and merge-path
+ * (rows + nonzeros split evenly by a search along diagonals of the merge of
+ * row ends and atom indices, with a carry-out fix-up, Sec. 5.2.1).
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers are DEVICE pointers unless the argument name starts with `host_`.
+ *    The caller owns every buffer it passes; the plan owns what it allocates
+ *    (split tables, carry slots, the cached transpose) and frees it in
+ *    lb_plan_destroy.  A plan keeps `tile_offsets` by pointer: that buffer must
+ *    stay alive and unchanged while the plan is used.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *  - Results are OVERWRITTEN, never accumulated (Listing 3 writes y[row] = sum).
+ *    Empty tiles give +0.0f.
+ *  - lb_spmv / lb_spmv_backward (after lb_prepare_backward) / lb_batch_spmv /
+ *    lb_batch_spmv_backward (after lb_batch_prepare_backward) are asynchronous:
+ *    they allocate nothing and never synchronise, so they may be captured in a
+ *    CUDA graph.  lb_plan*, lb_prepare_backward, lb_batch_plan and
+ *    lb_batch_prepare_backward allocate and synchronise `stream`.
+ *  - Results are deterministic: the same plan and inputs give bit-identical
+ *    outputs on every call (no floating-point atomics anywhere).
+ *  - One plan serves one stream at a time: its carry slots and fix-up ticket are
+ *    shared by its calls, so calls on the same plan that overlap on the GPU race.
+ *  - Errors are returned as lb_status_t; nothing traps on the device and no
+ *    exception crosses the ABI.  lb_last_error() gives a one-line detail for the
+ *    calling thread's last failure.
+ */
+#ifndef LB_H_
+#define LB_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lb_status_t {
+  LB_OK = 0,
+  LB_ERR_INVALID_ARG = 1,  /* bad size, null pointer, malformed tile_offsets (when validated) */
+  LB_ERR_CUDA = 2,         /* a CUDA runtime call failed; see lb_last_error() */
+  LB_ERR_OOM = 3,          /* device allocation failed */
+  LB_ERR_UNSUPPORTED = 4,  /* option combination not built (e.g. group size not a power of two) */
+  LB_ERR_TIMEOUT = 5,      /* reserved: no kernel in this library waits on another block */
+  LB_ERR_BAD_INPUT = 6     /* a validated kernel saw a column index outside [0, num_cols) */
+} lb_status_t;
+
+typedef enum lb_schedule_t {
+  LB_THREAD_MAPPED = 0, /* Sec. 4.2, Listing 2: tile t to thread t, grid-stride */
+  LB_WARP_MAPPED = 1,   /* Sec. 5.2.2-5.2.3: group-mapped with a group of 32 threads */
+  LB_BLOCK_MAPPED = 2,  /* Sec. 5.2.2-5.2.3: group-mapped with a group of one thread block */
+  LB_MERGE_PATH = 3,    /* Sec. 5.2.1: even split of rows + atoms, carry-out fix-up */
+  LB_GROUP_MAPPED = 4,  /* Sec. 5.2.3: group of lb_plan_opts_t.group_size threads (4..256, power of 2) */
+  LB_AUTO = 5           /* Sec. 6.2 heuristic: merge-path unless (rows < 500 or cols < 500) and
+                           atoms < 10000, then thread-mapped (see lb_heuristic_schedule) */
+} lb_schedule_t;
+
+typedef struct lb_plan_s* lb_plan_t;
+
+/* Plan options.  Zero means "default" for every field. */
+typedef struct lb_plan_opts_t {
+  int32_t num_cols;         /* columns of A; needed by LB_AUTO and by column validation (0 = unknown) */
+  int32_t items_per_thread; /* merge-path: rows + atoms per thread per tile, one of 4, 8, 16 (default 8) */
+  int32_t group_size;       /* LB_GROUP_MAPPED: threads per group (default 32) */
+  int32_t ctas_per_sm;      /* merge-path: resident CTAs per SM for the persistent grid (default: occupancy) */
+  int32_t validate;         /* nonzero: lb_plan checks tile_offsets on the device (tile_offsets[0] = 0,
+                               nondecreasing, last = num_atoms -> LB_ERR_INVALID_ARG); kernels check every
+                               column index against num_cols and record LB_ERR_BAD_INPUT for lb_status */
+  int32_t reserved[3];
+} lb_plan_opts_t;
+
+/* What a plan resolved to (for tests, the autotuner and reporting). */
+typedef struct lb_plan_info_t {
+  int32_t schedule;         /* resolved lb_schedule_t (never LB_AUTO) */
+  int32_t num_tiles, num_cols;
+  int64_t num_atoms;
+  int32_t block_threads;    /* threads per CTA */
+  int32_t grid;             /* CTAs launched per SpMV */
+  int32_t items_per_tile;   /* merge-path: rows + atoms staged per CTA tile (block_threads * items_per_thread) */
+  int32_t tiles_per_cta;    /* merge-path: tiles walked by each persistent CTA */
+  int64_t num_splits;       /* merge-path: entries in the split table */
+  int32_t group_size;       /* group-mapped schedules */
+  int32_t num_sms;
+  int32_t kernels_per_spmv; /* launches one lb_spmv issues */
+  int32_t has_transpose;    /* lb_prepare_backward done */
+} lb_plan_info_t;
+
+/* ------------------------------------------------------------------ plans -- */
+
+/*
+ * Builds a plan for SpMV over the tile set given by `tile_offsets` (device,
+ * int32, num_tiles + 1 entries) with `num_atoms` atoms, under `schedule`.
+ * For LB_MERGE_PATH this runs the setup step of Sec. 5.2.1 once, on the device:
+ * the persistent grid's CTA ranges (equal shares of rows + atoms) are cut into
+ * tiles of items_per_tile merge items and the (row, atom) split of every tile
+ * boundary diagonal is found by bisection and stored in the plan.
+ * Errors: LB_ERR_INVALID_ARG (negative sizes, null out/tile_offsets with
+ * num_tiles > 0, malformed offsets when validated), LB_ERR_OOM, LB_ERR_CUDA.
+ * Synchronises `stream` (lb_plan uses the legacy default stream).
+ */
+lb_status_t lb_plan(lb_plan_t* out, const int32_t* tile_offsets, int32_t num_tiles, int32_t num_atoms,
+                    lb_schedule_t schedule);
+lb_status_t lb_plan_ex(lb_plan_t* out, const int32_t* tile_offsets, int32_t num_tiles, int32_t num_atoms,
+                       lb_schedule_t schedule, const lb_plan_opts_t* opts, void* stream);
+void lb_plan_destroy(lb_plan_t plan);
+lb_status_t lb_plan_get_info(lb_plan_t plan, lb_plan_info_t* info);
+
+/*
+ * Copies the merge-path split table to host memory: host_diag[q] is a diagonal
+ * of the merged list of row ends and atoms, (host_ij[2q], host_ij[2q+1]) its
+ * (row, atom) split (Sec. 5.2.1; a row end precedes the atom with the same
+ * index).  `which` = 0 for the forward tile set, 1 for the transposed one built
+ * by lb_prepare_backward.  Writes min(count, cap) entries and the full count to
+ * *count.  LB_ERR_INVALID_ARG if the plan is not merge-path or the table does
+ * not exist.  Synchronous.
+ */
+lb_status_t lb_plan_splits(lb_plan_t plan, int32_t which, int64_t* host_diag, int32_t* host_ij, size_t cap,
+                           size_t* count);
+
+/* ------------------------------------------------------------------- SpMV -- */
+
+/*
+ * y = A x (Sec. 1; Listing 3): y[t] = sum over atoms k of tile t of
+ * vals[k] * x[col_idx[k]], computed in FP32 by the plan's schedule.
+ * col_idx: int32 [num_atoms]; vals: float [num_atoms]; x: float [num_cols];
+ * y: float [num_tiles], overwritten.  16-byte aligned col_idx/vals take the
+ * 128-bit load path; any other alignment is accepted.  No allocation, no sync.
+ * Errors: LB_ERR_INVALID_ARG (null pointer with num_atoms > 0), LB_ERR_CUDA
+ * (launch failure).  Out-of-range column indices are undefined behaviour unless
+ * the plan validates (then they read as 0 and lb_status reports them).
+ */
+lb_status_t lb_spmv(lb_plan_t plan, const int32_t* col_idx, const float* vals, const float* x, float* y,
+                    void* stream);
+
+/*
+ * Builds and caches A's transpose for the backward pass: a stable counting sort
+ * of the atoms by column (histogram, exclusive scan, stable scatter), giving
+ * CSC offsets cp[num_cols + 1], the row of each CSC slot riT[num_atoms] and the
+ * source atom perm[num_atoms]; rows ascend within each column, bit-exactly.
+ * Also plans the same schedule over the transposed tile set (tiles = columns).
+ * Allocates, synchronises `stream`.  Called implicitly by the first
+ * lb_spmv_backward that asks for dx.  Errors: LB_ERR_INVALID_ARG, LB_ERR_OOM,
+ * LB_ERR_CUDA.
+ */
+lb_status_t lb_prepare_backward(lb_plan_t plan, int32_t num_cols, const int32_t* col_idx, void* stream);
+
+/* Copies the cached transpose into caller buffers cp[num_cols+1], riT[num_atoms], perm[num_atoms]. */
+lb_status_t lb_plan_transpose(lb_plan_t plan, int32_t* cp, int32_t* riT, int32_t* perm, void* stream);
+
+/*
+ * Gradients of y = A x for an upstream gradient dy = dL/dy (float [num_tiles]):
+ *   dx[c]    = sum over atoms k in column c of vals[k] * dy[row(k)]  (dx = A^T dy),
+ *              float [num_cols], run by the plan's schedule over the cached
+ *              transpose (values gathered through perm);
+ *   dvals[k] = dy[row(k)] * x[col_idx[k]], float [num_atoms], one FP32 product per
+ *              atom, row(k) taken from the merge-path walk.
+ * Either output may be NULL to skip it.  Overwrites.  No allocation or sync once
+ * lb_prepare_backward has run for the same num_cols.
+ */
+lb_status_t lb_spmv_backward(lb_plan_t plan, int32_t num_cols, const int32_t* col_idx, const float* vals,
+                             const float* x, const float* dy, float* dx, float* dvals, void* stream);
+
+/*
+ * Tile of every atom (the schedule's get_tile applied to all atoms, Sec. 5.2.3):
+ * tile_of_atom[k] = t with tile_offsets[t] <= k < tile_offsets[t+1], int32
+ * [num_atoms], found by the merge-path walk.  Async, no allocation.
+ */
+lb_status_t lb_atom_tiles(lb_plan_t plan, int32_t* tile_of_atom, void* stream);
+
+/*
+ * Synchronises `stream`, then reads and clears the plan's device error word:
+ * LB_OK, or LB_ERR_BAD_INPUT if a validated kernel met a column index outside
+ * [0, num_cols) since the last call.
+ */
+lb_status_t lb_status(lb_plan_t plan, void* stream);
+
+/* -------------------------------------------------------------- batching -- */
+
+/*
+ * Plan for a batch of `num_mats` CSR matrices run as ONE persistent merge-path
+ * launch (the work-oriented schedule of Sec. 5.2.1 applied to the block-diagonal
+ * concatenation, in persistent-kernel style, Sec. 5.1).  Sizes are host arrays
+ * host_rows[m], host_cols[m], host_nnz[m].  rp_cat (device, int32) holds the
+ * matrices' own row offsets back to back (host_rows[m] + 1 entries each, each
+ * starting at 0).  The batch's data buffers are concatenations in matrix order:
+ * col_idx/vals by atoms (sum nnz), x by columns (sum cols), y by rows (sum rows).
+ * Global diagonals and offsets are int64.  The split table stores the matrix of
+ * every split.  Allocates, synchronises `stream`.
+ */
+lb_status_t lb_batch_plan(lb_plan_t* out, int32_t num_mats, const int32_t* host_rows, const int32_t* host_cols,
+                          const int64_t* host_nnz, const int32_t* rp_cat, const lb_plan_opts_t* opts, void* stream);
+
+/* y_cat = blockdiag(A_m) x_cat in one launch.  Async, no allocation. */
+lb_status_t lb_batch_spmv(lb_plan_t plan, const int32_t* col_cat, const float* vals_cat, const float* x_cat,
+                          float* y_cat, void* stream);
+
+/* Builds and caches every matrix's transpose and the batched merge-path plan over them. */
+lb_status_t lb_batch_prepare_backward(lb_plan_t plan, const int32_t* col_cat, void* stream);
+
+/* dx_cat = blockdiag(A_m^T) dy_cat and dvals_cat = dy[row] * x[col], each one launch; NULL skips. */
+lb_status_t lb_batch_spmv_backward(lb_plan_t plan, const int32_t* col_cat, const float* vals_cat,
+                                   const float* x_cat, const float* dy_cat, float* dx_cat, float* dvals_cat,
+                                   void* stream);
+
+/* ------------------------------------------------------------ host logic -- */
+
+/*
+ * The schedule the Sec. 6.2 heuristic picks: merge-path unless
+ * (rows < 500 or cols < 500) and nnz < 10000, in which case thread-mapped.
+ * Pure host function.
+ */
+lb_schedule_t lb_heuristic_schedule(int32_t rows, int32_t cols, int64_t nnz);
+
+/*
+ * The diagonals a merge-path plan splits at, as a pure host function:
+ * `grid` persistent CTAs take equal shares [floor(c*items/grid),
+ * floor((c+1)*items/grid)) of the items = rows + atoms, each share cut into
+ * tiles of items_per_tile; entry c*(tiles_per_cta+1)+k is
+ * min(share_begin(c) + k*items_per_tile, share_end(c)), with
+ * tiles_per_cta = ceil(max share / items_per_tile).  Writes min(count, cap)
+ * diagonals to host_diag and the total count to *count.
+ */
+lb_status_t lb_merge_diagonals(int64_t items, int32_t grid, int32_t items_per_tile, int64_t* host_diag, size_t cap,
+                               size_t* count, int32_t* tiles_per_cta);
+
+const char* lb_status_string(lb_status_t status);
+const char* lb_last_error(void);
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int32_t lb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LB_H_ */

@@ -1,0 +1,93 @@
+"""ctypes binding of ``liblb.so``: argument marshalling only.
+
+Every function here forwards to the C ABI in ``include/lb.h``; all work runs in
+the library's CUDA kernels.  If the library is missing, importing the binding
+raises: there is no CPU or PyTorch fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import buildlib as _build
+
+_lib = None
+
+
+class LBError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}" + (f" ({detail})" if detail else ""))
+
+
+STATUS_NAMES = {0: "LB_OK", 1: "LB_ERR_INVALID_ARG", 2: "LB_ERR_CUDA", 3: "LB_ERR_OOM", 4: "LB_ERR_UNSUPPORTED",
+                5: "LB_ERR_TIMEOUT", 6: "LB_ERR_BAD_INPUT"}
+
+
+class PlanOpts(ctypes.Structure):
+    _fields_ = [("num_cols", ctypes.c_int32), ("items_per_thread", ctypes.c_int32), ("group_size", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("validate", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("schedule", ctypes.c_int32), ("num_tiles", ctypes.c_int32), ("num_cols", ctypes.c_int32),
+                ("num_atoms", ctypes.c_int64), ("block_threads", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("items_per_tile", ctypes.c_int32), ("tiles_per_cta", ctypes.c_int32), ("num_splits", ctypes.c_int64),
+                ("group_size", ctypes.c_int32), ("num_sms", ctypes.c_int32), ("kernels_per_spmv", ctypes.c_int32),
+                ("has_transpose", ctypes.c_int32)]
+
+
+# name -> (restype, argtypes); the declarations of include/lb.h
+VP, I32, I64, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+PLANP = ctypes.POINTER(ctypes.c_void_p)
+SIGNATURES = {
+    "lb_plan": (I32, [PLANP, VP, I32, I32, I32]),
+    "lb_plan_ex": (I32, [PLANP, VP, I32, I32, I32, ctypes.POINTER(PlanOpts), VP]),
+    "lb_plan_destroy": (None, [VP]),
+    "lb_plan_get_info": (I32, [VP, ctypes.POINTER(PlanInfo)]),
+    "lb_plan_splits": (I32, [VP, I32, VP, VP, SZ, ctypes.POINTER(SZ)]),
+    "lb_spmv": (I32, [VP, VP, VP, VP, VP, VP]),
+    "lb_prepare_backward": (I32, [VP, I32, VP, VP]),
+    "lb_plan_transpose": (I32, [VP, VP, VP, VP, VP]),
+    "lb_spmv_backward": (I32, [VP, I32, VP, VP, VP, VP, VP, VP, VP]),
+    "lb_atom_tiles": (I32, [VP, VP, VP]),
+    "lb_status": (I32, [VP, VP]),
+    "lb_batch_plan": (I32, [PLANP, I32, VP, VP, VP, VP, ctypes.POINTER(PlanOpts), VP]),
+    "lb_batch_spmv": (I32, [VP, VP, VP, VP, VP, VP]),
+    "lb_batch_prepare_backward": (I32, [VP, VP, VP]),
+    "lb_batch_spmv_backward": (I32, [VP, VP, VP, VP, VP, VP, VP, VP]),
+    "lb_heuristic_schedule": (I32, [I32, I32, I64]),
+    "lb_merge_diagonals": (I32, [I64, I32, I32, VP, SZ, ctypes.POINTER(SZ), ctypes.POINTER(I32)]),
+    "lb_status_string": (ctypes.c_char_p, [I32]),
+    "lb_last_error": (ctypes.c_char_p, []),
+    "lb_version": (I32, []),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load liblb.so (building it in-tree first if sources changed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"liblb.so not found at {path}: build it with paper_2301_04792_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(status: int, where: str):
+    if status != 0:
+        lib = load()
+        raise LBError(status, where, lib.lb_last_error().decode(errors="replace"))

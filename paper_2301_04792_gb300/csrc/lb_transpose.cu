@@ -1,0 +1,246 @@
+// CSR -> CSC transpose by a stable counting sort of the atoms by column, run on
+// the device without floating point and without order-dependent atomics:
+//   cp   = inclusive scan of a column histogram (integer atomics: the final
+//          counts do not depend on their order),
+//   perm = source atom of every CSC slot, from a stable LSD radix sort of the
+//          (column, atom) pairs in 8-bit digits: per 4096-atom tile a digit
+//          histogram, one exclusive scan over (digit, tile), then a stable
+//          scatter in which each atom's rank among equal digits follows its
+//          position (warp ranks from __match_any_sync, warps and rounds in
+//          order),
+//   riT  = row of the source atom, gathered from the atom->row map.
+// Rows therefore ascend within every column and the result is bit-exact.
+#include <algorithm>
+
+#include "lb_internal.h"
+
+namespace lbh {
+
+namespace {
+
+constexpr int kScanBlock = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanBlock * kScanItems;
+
+constexpr int kRadixBlock = 256;
+constexpr int kRadixItems = 16;
+constexpr int kRadixTile = kRadixBlock * kRadixItems;
+constexpr int kRadixWarps = kRadixBlock / 32;
+
+__device__ __forceinline__ int block_incl_scan_int(int v, int* s_w) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += n;
+  }
+  if (lane == 31) s_w[warp] = v;
+  __syncthreads();
+  int before = 0;
+  for (int w = 0; w < warp; ++w) before += s_w[w];
+  __syncthreads();
+  return v + before;
+}
+
+// per-tile totals
+__global__ void scan_reduce_kernel(const int32_t* __restrict__ in, int64_t n, int32_t* __restrict__ sums) {
+  __shared__ int s_w[kScanBlock / 32];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  int acc = 0;
+#pragma unroll
+  for (int r = 0; r < kScanItems; ++r) {
+    const int64_t i = base + (int64_t)r * kScanBlock + threadIdx.x;
+    if (i < n) acc += in[i];
+  }
+  const int tot = block_incl_scan_int(acc, s_w);
+  if (threadIdx.x == kScanBlock - 1) sums[blockIdx.x] = tot;
+}
+
+// scan of one tile (blocked: thread t owns items [t*16, t*16+16)) plus the tile's prefix
+__global__ void scan_apply_kernel(const int32_t* __restrict__ in, int32_t* __restrict__ out, int64_t n,
+                                  const int32_t* __restrict__ prefix, int inclusive) {
+  __shared__ int s_w[kScanBlock / 32];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  int v[kScanItems];
+  int acc = 0;
+#pragma unroll
+  for (int r = 0; r < kScanItems; ++r) {
+    const int64_t i = base + r;
+    v[r] = i < n ? in[i] : 0;
+    acc += v[r];
+  }
+  const int incl = block_incl_scan_int(acc, s_w);
+  int run = incl - acc + (prefix ? prefix[blockIdx.x] : 0);
+#pragma unroll
+  for (int r = 0; r < kScanItems; ++r) {
+    const int64_t i = base + r;
+    const int x = v[r];
+    if (i < n) out[i] = inclusive ? run + x : run;
+    run += x;
+  }
+}
+
+__global__ void histogram_kernel(const int32_t* __restrict__ keys, int64_t n, int32_t* __restrict__ cnt) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(cnt + keys[i], 1);
+}
+
+__global__ void radix_upsweep_kernel(const int32_t* __restrict__ keys, int64_t n, int shift, int32_t* __restrict__ hist,
+                                     int64_t ntiles) {
+  __shared__ int s_cnt[256];
+  s_cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+#pragma unroll 4
+  for (int r = 0; r < kRadixItems; ++r) {
+    const int64_t i = base + (int64_t)r * kRadixBlock + threadIdx.x;
+    if (i < n) atomicAdd(&s_cnt[(keys[i] >> shift) & 255], 1);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = s_cnt[threadIdx.x];
+}
+
+// Stable scatter of one tile.  Atoms are visited in index order: round r holds
+// atoms base + r*256 + [0, 256), warp w its 32 lanes.  An atom's position is the
+// tile's base for its digit + atoms of that digit in earlier rounds + in earlier
+// warps of this round + in earlier lanes of its warp.
+__global__ void radix_downsweep_kernel(const int32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in,
+                                       int64_t n, int shift, const int32_t* __restrict__ hist_scan, int64_t ntiles,
+                                       int32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out) {
+  __shared__ int s_base[256];
+  __shared__ int s_run[256];
+  __shared__ int s_wc[kRadixWarps][256];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  s_base[tid] = hist_scan[(int64_t)tid * ntiles + blockIdx.x];
+  s_run[tid] = 0;
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+  for (int r = 0; r < kRadixItems; ++r) {
+#pragma unroll
+    for (int w = 0; w < kRadixWarps; ++w) s_wc[w][tid] = 0;
+    __syncthreads();
+    const int64_t i = base + (int64_t)r * kRadixBlock + tid;
+    const bool valid = i < n;
+    const int key = valid ? keys_in[i] : 0;
+    const int val = valid ? (vals_in ? vals_in[i] : (int)i) : 0;
+    const int d = valid ? ((key >> shift) & 255) : 256;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const int rank = __popc(peers & lt);
+    if (valid && rank == 0) s_wc[warp][d] = __popc(peers);
+    __syncthreads();
+    {
+      int run = s_run[tid];
+#pragma unroll
+      for (int w = 0; w < kRadixWarps; ++w) {
+        const int c = s_wc[w][tid];
+        s_wc[w][tid] = run;
+        run += c;
+      }
+      s_run[tid] = run;
+    }
+    __syncthreads();
+    if (valid) {
+      const int pos = s_base[d] + s_wc[warp][d] + rank;
+      keys_out[pos] = key;
+      vals_out[pos] = val;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void gather_kernel(const int32_t* __restrict__ src, const int32_t* __restrict__ idx, int64_t n,
+                              int32_t* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = src[idx[i]];
+}
+
+__global__ void iota_kernel(int32_t* out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (int32_t)i;
+}
+
+unsigned grid_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b > 65536 * 8) b = 65536 * 8;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() { cudaFree(p); }
+};
+
+}  // namespace
+
+lb_status_t device_scan(const int32_t* in, int32_t* out, int64_t n, bool inclusive, cudaStream_t s) {
+  if (n <= 0) return LB_OK;
+  const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+  if (tiles == 1) {
+    scan_apply_kernel<<<1, kScanBlock, 0, s>>>(in, out, n, nullptr, inclusive ? 1 : 0);
+    LB_CUDA_TRY(cudaGetLastError());
+    return LB_OK;
+  }
+  DevBuf sums;
+  LB_CUDA_TRY(cudaMalloc(&sums.p, sizeof(int32_t) * (size_t)tiles));
+  int32_t* ps = static_cast<int32_t*>(sums.p);
+  scan_reduce_kernel<<<(unsigned)tiles, kScanBlock, 0, s>>>(in, n, ps);
+  LB_CUDA_TRY(cudaGetLastError());
+  LB_TRY(device_scan(ps, ps, tiles, false, s));
+  scan_apply_kernel<<<(unsigned)tiles, kScanBlock, 0, s>>>(in, out, n, ps, inclusive ? 1 : 0);
+  LB_CUDA_TRY(cudaGetLastError());
+  // `sums` is freed when this returns; make sure the kernels using it are done
+  LB_CUDA_TRY(cudaStreamSynchronize(s));
+  return LB_OK;
+}
+
+lb_status_t transpose_sort(const int32_t* keys, const int32_t* row_of, int64_t N, int32_t C, int32_t* cp,
+                           int32_t* riT, int32_t* perm, cudaStream_t s) {
+  // cp: histogram of keys into cp[1..C], then inclusive scan
+  LB_CUDA_TRY(cudaMemsetAsync(cp, 0, sizeof(int32_t) * ((size_t)C + 1), s));
+  if (N == 0) return LB_OK;
+  histogram_kernel<<<grid_for(N, 256), 256, 0, s>>>(keys, N, cp + 1);
+  LB_CUDA_TRY(cudaGetLastError());
+  LB_TRY(device_scan(cp + 1, cp + 1, C, true, s));
+
+  int bits = 0;
+  while (bits < 31 && ((int64_t)1 << bits) < (int64_t)C) ++bits;
+  const int passes = (bits + 7) / 8;
+  if (passes == 0) {
+    iota_kernel<<<grid_for(N, 256), 256, 0, s>>>(perm, N);
+    LB_CUDA_TRY(cudaGetLastError());
+  } else {
+    const int64_t ntiles = (N + kRadixTile - 1) / kRadixTile;
+    DevBuf ka, kb, va, vb, hist;
+    LB_CUDA_TRY(cudaMalloc(&ka.p, sizeof(int32_t) * (size_t)N));
+    LB_CUDA_TRY(cudaMalloc(&kb.p, sizeof(int32_t) * (size_t)N));
+    LB_CUDA_TRY(cudaMalloc(&va.p, sizeof(int32_t) * (size_t)N));
+    LB_CUDA_TRY(cudaMalloc(&vb.p, sizeof(int32_t) * (size_t)N));
+    LB_CUDA_TRY(cudaMalloc(&hist.p, sizeof(int32_t) * (size_t)(256 * ntiles)));
+    const int32_t* kin = keys;
+    const int32_t* vin = nullptr;  // first pass: values are the atom indices
+    int32_t* kbuf[2] = {static_cast<int32_t*>(ka.p), static_cast<int32_t*>(kb.p)};
+    int32_t* vbuf[2] = {static_cast<int32_t*>(va.p), static_cast<int32_t*>(vb.p)};
+    for (int p = 0; p < passes; ++p) {
+      const int shift = 8 * p;
+      int32_t* kout = kbuf[p & 1];
+      int32_t* vout = (p == passes - 1) ? perm : vbuf[p & 1];
+      radix_upsweep_kernel<<<(unsigned)ntiles, kRadixBlock, 0, s>>>(kin, N, shift, static_cast<int32_t*>(hist.p),
+                                                                    ntiles);
+      LB_CUDA_TRY(cudaGetLastError());
+      LB_TRY(device_scan(static_cast<int32_t*>(hist.p), static_cast<int32_t*>(hist.p), 256 * ntiles, false, s));
+      radix_downsweep_kernel<<<(unsigned)ntiles, kRadixBlock, 0, s>>>(
+          kin, vin, N, shift, static_cast<int32_t*>(hist.p), ntiles, kout, vout);
+      LB_CUDA_TRY(cudaGetLastError());
+      kin = kout;
+      vin = vout;
+    }
+    LB_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  gather_kernel<<<grid_for(N, 256), 256, 0, s>>>(row_of, perm, N, riT);
+  LB_CUDA_TRY(cudaGetLastError());
+  LB_CUDA_TRY(cudaStreamSynchronize(s));
+  return LB_OK;
+}
+
+}  // namespace lbh

@@ -1,0 +1,87 @@
+"""The C ABI library builds, loads without a GPU and exports every symbol the header declares.
+
+Only host-side functions are called here (no GPU needed): the Sec. 6.2
+schedule heuristic and the merge-path diagonal layout.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2301_04792_gb300 import _lib, buildlib as lb_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\**\s+(lb_[a-z_0-9]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    lb_build.build()
+    return _lib.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("lb_plan", "lb_spmv", "lb_spmv_backward", "lb_plan_destroy", "lb_batch_plan",
+                     "lb_batch_spmv", "lb_batch_spmv_backward", "lb_status", "lb_plan_splits", "lb_plan_transpose"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    raw = ctypes.CDLL(_lib.library_path())
+    missing = [n for n in declared_functions() if not hasattr(raw, n)]
+    assert not missing, missing
+    # and the binding's signature table covers the header exactly
+    assert sorted(_lib.SIGNATURES) == declared_functions()
+
+
+def test_version_and_status_strings(lib):
+    assert lib.lb_version() >= 10000
+    for s in range(7):
+        assert lib.lb_status_string(s).decode().startswith(_lib.STATUS_NAMES[s])
+
+
+def test_heuristic_matches_sec_6_2(lib):
+    # merge-path unless (rows < 500 or cols < 500) and nnz < 10000
+    TM, MP = 0, 3
+    assert lib.lb_heuristic_schedule(499, 10 ** 6, 9999) == TM
+    assert lib.lb_heuristic_schedule(10 ** 6, 499, 9999) == TM
+    assert lib.lb_heuristic_schedule(499, 499, 10000) == MP
+    assert lib.lb_heuristic_schedule(500, 500, 5) == MP
+    assert lib.lb_heuristic_schedule(2000, 2000, 20000) == MP
+
+
+@pytest.mark.parametrize("items,grid,ipt", [(0, 1, 2048), (1, 1, 2048), (21_000_000, 456, 2048),
+                                            (22_000, 86, 2048), (1000, 7, 3), (123457, 152, 1024)])
+def test_merge_diagonals_layout(lib, items, grid, ipt):
+    from paper_2301_04792_gb300 import merge_diagonals
+    d, tpc = merge_diagonals(items, grid, ipt)
+    assert d.shape[0] == grid * (tpc + 1)
+    d = d.reshape(grid, tpc + 1)
+    begins = np.array([c * items // grid for c in range(grid)])
+    ends = np.array([(c + 1) * items // grid for c in range(grid)])
+    assert np.array_equal(d[:, 0], begins) and np.array_equal(d[:, -1], ends)  # equal shares, contiguous
+    assert (np.diff(d, axis=1) >= 0).all() and (np.diff(d, axis=1) <= ipt).all()  # tiles of at most ipt items
+    assert d.min() >= 0 and d.max() <= items
+    # ceil(share / ipt) tiles suffice for the largest share
+    assert tpc == max(1, -(-(-(-items // grid)) // ipt))
+
+
+def test_merge_diagonals_rejects_bad_args(lib):
+    n = ctypes.c_size_t(0)
+    t = ctypes.c_int32(0)
+    assert lib.lb_merge_diagonals(-1, 1, 1, None, 0, ctypes.byref(n), ctypes.byref(t)) == 1
+    assert lib.lb_merge_diagonals(10, 0, 1, None, 0, ctypes.byref(n), ctypes.byref(t)) == 1
+    assert b"items" in lib.lb_last_error()

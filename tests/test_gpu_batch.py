@@ -1,0 +1,155 @@
+"""GPU parity of the batched persistent merge-path form (forward and backward),
+its CUDA-graph replay, and the batched workloads at full size."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from helpers import assert_within_bound, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbmod():
+    import paper_2301_04792_gb300 as lb
+    lb.build()
+    return lb
+
+
+def batch_inputs(b, seed=0):
+    xs = [W.x_for(m, seed=seed + i) for i, m in enumerate(b.mats)]
+    dys = [W.dy_for(m, seed=seed + i) for i, m in enumerate(b.mats)]
+    return xs, dys
+
+
+def oracle_batch(b, xs, dys):
+    y64, yb, dx64, dxb, dv = [], [], [], [], []
+    for m, x, dy in zip(b.mats, xs, dys):
+        y, bb = oracle.spmv(m.rp, m.ci, m.v, x)
+        d, db, g = oracle.grad(m.rp, m.ci, m.v, x, dy, m.num_cols)
+        y64.append(y), yb.append(bb), dx64.append(d), dxb.append(db), dv.append(g)
+    cat = lambda a, dt: np.concatenate(a).astype(dt) if a else np.zeros(0, dt)
+    return (cat(y64, np.float64), cat(yb, np.float64), cat(dx64, np.float64), cat(dxb, np.float64),
+            cat(dv, np.float32))
+
+
+def make_plan(lb, b, **kw):
+    rp_cat, ci, v = to_dev(b.rp_cat(), b.ci_cat(), b.v_cat())
+    plan = lb.BatchPlan(b.rows(), b.cols(), b.nnz(), rp_cat, **kw)
+    return plan, rp_cat, ci, v
+
+
+def check_batch(lb, b, ipts=(8,)):
+    import torch
+    xs, dys = batch_inputs(b)
+    y64, yb, dx64, dxb, dv32 = oracle_batch(b, xs, dys)
+    xd, dyd = to_dev(np.concatenate(xs), np.concatenate(dys))
+    row_of = np.concatenate([oracle.row_of_atom(m.rp) for m in b.mats])
+    for ipt in ipts:
+        plan, rp_cat, ci, v = make_plan(lb, b, items_per_thread=ipt)
+        ys = [plan.spmv(ci, v, xd) for _ in range(3)]
+        assert_within_bound(ys[0].cpu().numpy(), y64, yb, "batch y")
+        for y in ys[1:]:
+            assert torch.equal(y.view(torch.int32), ys[0].view(torch.int32))
+        tiles = plan.atom_tiles().cpu().numpy()
+        row_base = np.concatenate([[0], np.cumsum(b.rows())])[:-1]
+        mat_of_atom = np.repeat(np.arange(b.num), b.nnz())
+        assert np.array_equal(tiles - row_base[mat_of_atom], row_of)
+        outs = [plan.backward(ci, v, xd, dyd) for _ in range(2)]
+        dx, dvals = outs[0]
+        assert_within_bound(dx.cpu().numpy(), dx64, dxb, "batch dx")
+        assert np.array_equal(dvals.cpu().numpy().view(np.uint32), dv32.view(np.uint32))
+        assert torch.equal(outs[1][0].view(torch.int32), dx.view(torch.int32))
+
+
+def test_small_batch(lbmod):
+    b = W.batch(num=40, rmin=50, rmax=5000, mmin=1, mmax=64, seed=3)
+    check_batch(lbmod, b, ipts=(4, 8, 16))
+
+
+def test_batch_with_degenerate_members(lbmod):
+    mats = [W.from_lengths(np.zeros(5, np.int64), 3, seed=1),           # all-empty rows
+            W.from_lengths(np.array([1]), 1, seed=2),                   # 1x1
+            W.powerlaw(3000, 3000, 50_000, lmax=3000, plant_long=False, seed=3),
+            W.from_lengths(np.array([20000]), 30000, seed=4),           # one long row
+            W.from_lengths(np.ones(7, np.int64), 1, seed=5),            # one column
+            W.plain(300, 300, 3, seed=6)]
+    check_batch(lbmod, W.Batch(mats), ipts=(4, 16))
+
+
+def test_single_matrix_batch_equals_oracle(lbmod):
+    b = W.Batch([W.powerlaw(20000, 20000, 400_000, lmax=20000, plant_long=False, seed=9)])
+    check_batch(lbmod, b)
+
+
+def test_batched_graph_replay(lbmod):
+    """Forward + backward captured once in a CUDA graph and replayed give the same bits."""
+    import torch
+    b = W.batch(num=24, rmin=100, rmax=20000, seed=4)
+    xs, dys = batch_inputs(b)
+    y64, yb, dx64, dxb, dv32 = oracle_batch(b, xs, dys)
+    plan, rp_cat, ci, v = make_plan(lbmod, b)
+    xd, dyd = to_dev(np.concatenate(xs), np.concatenate(dys))
+    plan.prepare_backward(ci)
+    y = torch.empty(plan.total_rows, device="cuda")
+    dx = torch.empty(plan.total_cols, device="cuda")
+    dv = torch.empty(plan.total_nnz, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        plan.spmv(ci, v, xd, y)
+        plan.backward(ci, v, xd, dyd, dx_cat=dx, dvals_cat=dv)
+    torch.cuda.current_stream().wait_stream(s)
+    ref = (y.clone(), dx.clone(), dv.clone())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.spmv(ci, v, xd, y)
+        plan.backward(ci, v, xd, dyd, dx_cat=dx, dvals_cat=dv)
+    for _ in range(3):
+        y.zero_(), dx.zero_(), dv.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        for a, r in zip((y, dx, dv), ref):
+            assert torch.equal(a.view(torch.int32), r.view(torch.int32))
+    assert_within_bound(y.cpu().numpy(), y64, yb, "graph y")
+    assert_within_bound(dx.cpu().numpy(), dx64, dxb, "graph dx")
+
+
+def test_full_batch_512(lbmod):
+    """The 512-matrix batch at full size: forward on every row."""
+    import torch
+    b = W.batch()
+    xs = [W.x_for(m, seed=i) for i, m in enumerate(b.mats)]
+    y64 = np.concatenate([oracle.spmv(m.rp, m.ci, m.v, x)[0] for m, x in zip(b.mats, xs)])
+    yb = np.concatenate([oracle.spmv(m.rp, m.ci, m.v, x)[1] for m, x in zip(b.mats, xs)])
+    plan, rp_cat, ci, v = make_plan(lbmod, b)
+    xd = to_dev(np.concatenate(xs))[0]
+    y = plan.spmv(ci, v, xd)
+    y2 = plan.spmv(ci, v, xd)
+    assert_within_bound(y.cpu().numpy(), y64, yb, "batch512 y")
+    assert torch.equal(y.view(torch.int32), y2.view(torch.int32))
+
+
+def test_full_differentiable_batch_64(lbmod):
+    """64 power-law matrices of 2^20 rows (~16M nnz each): fwd + bwd on sampled matrices' rows
+    and columns, dvals bit-exact on sampled atoms."""
+    import torch
+    b = W.diff_batch()
+    xs, dys = batch_inputs(b)
+    plan, rp_cat, ci, v = make_plan(lbmod, b)
+    xd, dyd = to_dev(np.concatenate(xs), np.concatenate(dys))
+    y = plan.spmv(ci, v, xd).cpu().numpy()
+    dx, dvals = plan.backward(ci, v, xd, dyd)
+    dx, dvals = dx.cpu().numpy(), dvals.cpu().numpy()
+    rows, cols, nnz = b.rows(), b.cols(), b.nnz()
+    rb = np.concatenate([[0], np.cumsum(rows)])
+    cb = np.concatenate([[0], np.cumsum(cols)])
+    nb = np.concatenate([[0], np.cumsum(nnz)])
+    for mi in (0, 17, 63):
+        m = b.mats[mi]
+        y64, yb = oracle.spmv(m.rp, m.ci, m.v, xs[mi])
+        assert_within_bound(y[rb[mi]:rb[mi + 1]], y64, yb, f"diff y m{mi}")
+        dx64, dxb, dv32 = oracle.grad(m.rp, m.ci, m.v, xs[mi], dys[mi], m.num_cols)
+        assert_within_bound(dx[cb[mi]:cb[mi + 1]], dx64, dxb, f"diff dx m{mi}")
+        assert np.array_equal(dvals[nb[mi]:nb[mi + 1]].view(np.uint32), dv32.view(np.uint32))
