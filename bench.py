@@ -269,13 +269,13 @@ def bench_batched(torch, lb, W, device, reps=5):
     def plain_calls(stream_ptr):
         calls = []
         for p, rs, cs, ns, cm in plans:
-            civ = vp(ci.data_ptr() + i4 * ns.start)
-            vv = vp(v.data_ptr() + f4 * ns.start)
-            xv = vp(x.data_ptr() + f4 * cs.start)
-            yv = vp(y.data_ptr() + f4 * rs.start)
-            dyv = vp(dy.data_ptr() + f4 * rs.start)
-            dxv = vp(dx.data_ptr() + f4 * cs.start)
-            dvv = vp(dv.data_ptr() + f4 * ns.start)
+            civ = vp(ci.data_ptr() + i4 * int(ns.start))
+            vv = vp(v.data_ptr() + f4 * int(ns.start))
+            xv = vp(x.data_ptr() + f4 * int(cs.start))
+            yv = vp(y.data_ptr() + f4 * int(rs.start))
+            dyv = vp(dy.data_ptr() + f4 * int(rs.start))
+            dxv = vp(dx.data_ptr() + f4 * int(cs.start))
+            dvv = vp(dv.data_ptr() + f4 * int(ns.start))
             calls.append((p.handle, civ, vv, xv, yv, dyv, dxv, dvv, cm))
         sp_ = vp(stream_ptr)
 
@@ -440,15 +440,18 @@ def run_ours(args, ws, rank, local):
     achieved = byts / (kern_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": profiled_traffic(),
-                "peak_kind": f"{peak_kind} HBM copy", "kernel": "mp_spmv_kernel",
+                "peak_kind": f"{peak_kind} HBM copy", "kernel": "mp_spmv_tma_kernel",
                 "kernel_ms_median": round(kern_ms, 5), "frac_of_8TBps_spec": round(achieved / 8000.0, 4)}
 
+    print(f"[bench] merge-path {value:.1f} GB/s ({step_ms * 1e3:.2f} us/step), kernel {achieved:.1f} GB/s, "
+          f"parity {parity_ok}", file=sys.stderr, flush=True)
     # other schedules on the same matrix (Fig. 3-style comparison), per-launch events
     sched = {}
     if not args.quick and not args.ncu:
         for s, kw in (("thread_mapped", {}), ("warp_mapped", {}), ("block_mapped", {}),
                       ("group_mapped", {"group_size": 8}), ("merge_path", {"items_per_thread": 4}),
-                      ("merge_path", {"items_per_thread": 16})):
+                      ("merge_path", {"items_per_thread": 16}),
+                      ("merge_path", {"items_per_thread": 8, "mp_variant": 1})):
             ps = plans_for(s, **kw)
             ln = launcher(ps)
             for i in range(3):

@@ -78,7 +78,11 @@ typedef struct lb_plan_opts_t {
   int32_t validate;         /* nonzero: lb_plan checks tile_offsets on the device (tile_offsets[0] = 0,
                                nondecreasing, last = num_atoms -> LB_ERR_INVALID_ARG); kernels check every
                                column index against num_cols and record LB_ERR_BAD_INPUT for lb_status */
-  int32_t reserved[3];
+  int32_t mp_variant;       /* merge-path work split inside a CTA tile: 0 = rows and atoms dealt to the
+                               threads in two passes, streamed by bulk copies (needs 16-byte aligned
+                               buffers, else 1 is used); 1 = each thread searches its own diagonal and
+                               walks its IPT items in merge order (Sec. 5.2.1 per thread) */
+  int32_t reserved[2];
 } lb_plan_opts_t;
 
 /* What a plan resolved to (for tests, the autotuner and reporting). */
@@ -88,7 +92,7 @@ typedef struct lb_plan_info_t {
   int64_t num_atoms;
   int32_t block_threads;    /* threads per CTA */
   int32_t grid;             /* CTAs launched per SpMV */
-  int32_t items_per_tile;   /* merge-path: rows + atoms staged per CTA tile (block_threads * items_per_thread) */
+  int32_t items_per_tile;   /* merge-path: rows + atoms per CTA tile (block_threads * items_per_thread - 4) */
   int32_t tiles_per_cta;    /* merge-path: tiles walked by each persistent CTA */
   int64_t num_splits;       /* merge-path: entries in the split table */
   int32_t group_size;       /* group-mapped schedules */

@@ -146,9 +146,11 @@ lb_status_t lb_plan_ex(lb_plan_t* out, const int32_t* tile_offsets, int32_t num_
     return LB_ERR_INVALID_ARG;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0;
+  LB_CUDA_TRY(cudaGetDevice(&dev));
   lb_plan_s* p = new lb_plan_s();
   p->opts = o;
-  LB_CUDA_TRY(cudaGetDevice(&p->device));
+  p->device = dev;
   p->num_sms = device_sms(p->device);
   p->rp = tile_offsets;
   p->num_tiles = num_tiles;
@@ -193,8 +195,8 @@ lb_status_t lb_plan_ex(lb_plan_t* out, const int32_t* tile_offsets, int32_t num_
   }
   // The forward merge-path table serves the merge-path schedule and, for every
   // schedule, the atom->tile walk used by dvals and lb_atom_tiles.
-  lb_status_t st = build_mp_table_single(p->mp, tile_offsets, num_tiles, num_atoms, o.items_per_thread, p->num_sms,
-                                         o.ctas_per_sm, s);
+  lb_status_t st = build_mp_table(p->mp, tile_offsets, num_tiles, num_atoms, o.items_per_thread, o.mp_variant,
+                                  p->num_sms, o.ctas_per_sm, nullptr, s);
   if (st != LB_OK) return fail(st);
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
@@ -214,10 +216,8 @@ void lb_plan_destroy(lb_plan_t p) {
   if (!p) return;
   p->mp.release();
   free_transpose(p);
-  p->bs.release();
-  p->bs_t.release();
-  cudaFree(p->perm_t_local);
-  cudaFree(p->riT_local);
+  p->bb.release();
+  cudaFree(p->rp_global);
   cudaFree(p->d_status);
   delete p;
 }
@@ -229,9 +229,9 @@ lb_status_t lb_plan_get_info(lb_plan_t p, lb_plan_info_t* info) {
   }
   std::memset(info, 0, sizeof(*info));
   info->schedule = p->schedule;
-  info->num_tiles = p->is_batch ? (int32_t)p->bs.total_rows : p->num_tiles;
-  info->num_cols = p->is_batch ? (int32_t)p->bs.total_cols : p->num_cols;
-  info->num_atoms = p->is_batch ? p->bs.total_nnz : p->num_atoms;
+  info->num_tiles = p->num_tiles;
+  info->num_cols = p->num_cols;
+  info->num_atoms = p->num_atoms;
   info->block_threads = kBlock;
   info->items_per_tile = p->mp.items_per_tile;
   info->tiles_per_cta = p->mp.tiles_per_cta;
@@ -274,31 +274,7 @@ lb_status_t lb_plan_splits(lb_plan_t p, int32_t which, int64_t* host_diag, int32
   const size_t n = cap < (size_t)t.entries ? cap : (size_t)t.entries;
   if (n == 0) return LB_OK;
   if (host_diag) LB_CUDA_TRY(cudaMemcpy(host_diag, t.d_diag, sizeof(int64_t) * n, cudaMemcpyDeviceToHost));
-  if (host_ij) {
-    if (!t.batch) {
-      LB_CUDA_TRY(cudaMemcpy(host_ij, t.splits, sizeof(int32_t) * 2 * n, cudaMemcpyDeviceToHost));
-    } else {
-      struct S { int64_t i, j; int32_t m, pad; };
-      S* tmp = new S[n];
-      cudaError_t e = cudaMemcpy(tmp, t.splits, sizeof(S) * n, cudaMemcpyDeviceToHost);
-      if (e != cudaSuccess) {
-        delete[] tmp;
-        set_error(cudaGetErrorString(e));
-        return LB_ERR_CUDA;
-      }
-      bool fits = true;
-      for (size_t q = 0; q < n; ++q) {
-        if (tmp[q].i > INT32_MAX || tmp[q].j > INT32_MAX) fits = false;
-        host_ij[2 * q] = (int32_t)tmp[q].i;
-        host_ij[2 * q + 1] = (int32_t)tmp[q].j;
-      }
-      delete[] tmp;
-      if (!fits) {
-        set_error("lb_plan_splits: batch coordinates exceed int32");
-        return LB_ERR_UNSUPPORTED;
-      }
-    }
-  }
+  if (host_ij) LB_CUDA_TRY(cudaMemcpy(host_ij, t.splits, sizeof(int32_t) * 2 * n, cudaMemcpyDeviceToHost));
   return LB_OK;
 }
 
@@ -313,18 +289,16 @@ lb_status_t lb_spmv(lb_plan_t p, const int32_t* col_idx, const float* vals, cons
     return LB_ERR_INVALID_ARG;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int32_t check = p->opts.validate ? p->num_cols : 0;
+  SpmvCall c{p->rp, p->num_tiles, col_idx, vals, nullptr, x, y, p->opts.validate ? p->num_cols : 0, p->d_status};
   switch (p->schedule) {
     case LB_THREAD_MAPPED:
-      return launch_tm_spmv(p->rp, p->num_tiles, col_idx, vals, nullptr, x, y, check, p->d_status, p->num_sms, s);
+      return launch_tm_spmv(c, s);
     case LB_WARP_MAPPED:
     case LB_BLOCK_MAPPED:
     case LB_GROUP_MAPPED:
-      return launch_gm_spmv(p->group_size, p->rp, p->num_tiles, col_idx, vals, nullptr, x, y, check, p->d_status,
-                            p->num_sms, s);
+      return launch_gm_spmv(p->group_size, c, p->num_sms, s);
     case LB_MERGE_PATH:
-      return launch_mp_spmv(p->mp, p->rp, nullptr, col_idx, vals, nullptr, x, y, p->num_tiles, check,
-                            p->d_status, s);
+      return launch_mp_spmv(p->mp, c, s);
     default:
       set_error("lb_spmv: unknown schedule");
       return LB_ERR_INVALID_ARG;
@@ -350,7 +324,8 @@ lb_status_t lb_prepare_backward(lb_plan_t p, int32_t num_cols, const int32_t* co
   LB_CUDA_TRY(cudaMalloc(&p->perm, sizeof(int32_t) * (size_t)(N > 0 ? N : 1)));
   int32_t* row_of = nullptr;
   LB_CUDA_TRY(cudaMalloc(&row_of, sizeof(int32_t) * (size_t)(N > 0 ? N : 1)));
-  lb_status_t st = launch_mp_expand(p->mp, p->rp, nullptr, nullptr, nullptr, nullptr, nullptr, row_of, 0, nullptr, s);
+  SpmvCall c{p->rp, p->num_tiles, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr};
+  lb_status_t st = launch_mp_expand(p->mp, c, nullptr, nullptr, row_of, s);
   if (st == LB_OK) st = transpose_sort(col_idx, row_of, N, num_cols, p->cp, p->riT, p->perm, s);
   cudaStreamSynchronize(s);
   cudaFree(row_of);
@@ -358,8 +333,8 @@ lb_status_t lb_prepare_backward(lb_plan_t p, int32_t num_cols, const int32_t* co
     free_transpose(p);
     return st;
   }
-  st = build_mp_table_single(p->mp_t, p->cp, num_cols, N, p->opts.items_per_thread, p->num_sms, p->opts.ctas_per_sm,
-                             s);
+  st = build_mp_table(p->mp_t, p->cp, num_cols, N, p->opts.items_per_thread, p->opts.mp_variant, p->num_sms,
+                      p->opts.ctas_per_sm, nullptr, s);
   if (st != LB_OK) {
     free_transpose(p);
     return st;
@@ -404,19 +379,19 @@ lb_status_t lb_spmv_backward(lb_plan_t p, int32_t num_cols, const int32_t* col_i
     if (p->num_atoms == 0) {
       if (num_cols > 0) LB_CUDA_TRY(cudaMemsetAsync(dx, 0, sizeof(float) * (size_t)num_cols, s));
     } else {
+      // dx = A^T dy: the plan's schedule over the transposed tile set (tiles = columns)
+      SpmvCall c{p->cp, num_cols, p->riT, vals, p->perm, dy, dx, 0, p->d_status};
       switch (p->schedule) {
         case LB_THREAD_MAPPED:
-          LB_TRY(launch_tm_spmv(p->cp, num_cols, p->riT, vals, p->perm, dy, dx, 0, p->d_status, p->num_sms, s));
+          LB_TRY(launch_tm_spmv(c, s));
           break;
         case LB_WARP_MAPPED:
         case LB_BLOCK_MAPPED:
         case LB_GROUP_MAPPED:
-          LB_TRY(launch_gm_spmv(p->group_size, p->cp, num_cols, p->riT, vals, p->perm, dy, dx, 0, p->d_status,
-                                p->num_sms, s));
+          LB_TRY(launch_gm_spmv(p->group_size, c, p->num_sms, s));
           break;
         default:
-          LB_TRY(launch_mp_spmv(p->mp_t, p->cp, nullptr, p->riT, vals, p->perm, dy, dx, num_cols, 0, p->d_status,
-                                s));
+          LB_TRY(launch_mp_spmv(p->mp_t, c, s));
       }
     }
   }
@@ -425,21 +400,21 @@ lb_status_t lb_spmv_backward(lb_plan_t p, int32_t num_cols, const int32_t* col_i
       set_error("lb_spmv_backward: col_idx or x is NULL");
       return LB_ERR_INVALID_ARG;
     }
-    const int32_t check = p->opts.validate ? p->num_cols : 0;
-    LB_TRY(launch_mp_expand(p->mp, p->rp, nullptr, col_idx, x, dy, dvals, nullptr, check, p->d_status, s));
+    SpmvCall c{p->rp, p->num_tiles, col_idx, nullptr, nullptr, x, nullptr, p->opts.validate ? p->num_cols : 0,
+               p->d_status};
+    LB_TRY(launch_mp_expand(p->mp, c, dy, dvals, nullptr, s));
   }
   return LB_OK;
 }
 
 lb_status_t lb_atom_tiles(lb_plan_t p, int32_t* tile_of_atom, void* stream) {
-  if (!p || (!tile_of_atom && (p->is_batch ? p->bs.total_nnz : p->num_atoms) > 0)) {
+  if (!p || (!tile_of_atom && p->num_atoms > 0)) {
     set_error("lb_atom_tiles: NULL argument");
     return LB_ERR_INVALID_ARG;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (p->is_batch)
-    return launch_mp_expand(p->mp, nullptr, &p->bs, nullptr, nullptr, nullptr, nullptr, tile_of_atom, 0, nullptr, s);
-  return launch_mp_expand(p->mp, p->rp, nullptr, nullptr, nullptr, nullptr, nullptr, tile_of_atom, 0, nullptr, s);
+  SpmvCall c{p->rp, p->num_tiles, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr};
+  return launch_mp_expand(p->mp, c, nullptr, nullptr, tile_of_atom, s);
 }
 
 lb_status_t lb_status(lb_plan_t p, void* stream) {
@@ -452,6 +427,10 @@ lb_status_t lb_status(lb_plan_t p, void* stream) {
   LB_CUDA_TRY(cudaStreamSynchronize(s));
   LB_CUDA_TRY(cudaMemcpy(&h, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   LB_CUDA_TRY(cudaMemset(p->d_status, 0, sizeof(int)));
+  if (h & 2) {
+    set_error("a bounded wait in a kernel gave up (results of that call are invalid)");
+    return LB_ERR_TIMEOUT;
+  }
   if (h) {
     set_error("a validated kernel saw a column index outside [0, num_cols)");
     return LB_ERR_BAD_INPUT;

@@ -29,38 +29,50 @@ void set_error(const std::string& msg);
 
 constexpr int kBlock = 256;
 
-// Merge-path split table for one tile set (Sec. 5.2.1 setup step, done once
-// per plan): `grid` persistent CTAs, each with tiles_per_cta tiles of
-// items_per_tile merge items; entry c*(tiles_per_cta+1)+k is the split at the
-// start of CTA c's k-th tile.
+// Merge-path split table for one tile set (the setup step of Sec. 5.2.1, done
+// once per plan): `grid` persistent CTAs, each with tiles_per_cta tiles of
+// items_per_tile merge items; entry c*(tiles_per_cta+1)+k is the (row, atom)
+// split at the start of CTA c's k-th tile.  For a batch, split_m[e] is the
+// matrix holding the split's atom.
 struct MpTable {
   bool built = false;
-  bool batch = false;
   int ipt = 8;
+  int variant = 0;  // lb_plan_opts_t.mp_variant
   int items_per_tile = 0;
   int grid = 0;
   int tiles_per_cta = 0;
   int64_t entries = 0;
   int64_t items = 0;
-  void* splits = nullptr;      // int2 (single) or lbk::Split64 (batch)
-  int64_t* d_diag = nullptr;   // diagonal of every entry (kept for lb_plan_splits)
+  int32_t num_tiles = 0;
+  int2* splits = nullptr;
+  int64_t* d_diag = nullptr;  // diagonal of every entry (kept for lb_plan_splits)
+  int32_t* split_m = nullptr;
   float* carry_val = nullptr;
-  int64_t* carry_row = nullptr;
+  int32_t* carry_row = nullptr;
   unsigned* ticket = nullptr;
   void release();
 };
 
-// Batched tile-set description (device copies of the per-matrix bases).
-struct BatchSet {
+// Per-matrix bases of a batch (device arrays of num + 1 entries).
+struct BatchBases {
   int32_t num = 0;
-  int64_t total_rows = 0, total_cols = 0, total_nnz = 0;
-  const int32_t* rp_cat = nullptr;  // caller-owned (forward) or plan-owned (transpose)
-  int64_t* row_base = nullptr;      // [num+1] device
-  int64_t* nnz_base = nullptr;      // [num+1]
-  int64_t* vec_base = nullptr;      // [num+1]
-  int64_t* diag_base = nullptr;     // [num+1] prefix of rows + nnz
-  bool owns_rp = false;
+  int64_t* nnz_base = nullptr;  // first atom of each matrix
+  int64_t* vec_base = nullptr;  // first dense-vector entry (column) of each matrix
   void release();
+};
+
+// What a kernel reads for one SpMV over a tile set.
+struct SpmvCall {
+  const int32_t* rp;      // row offsets of the tile set
+  int32_t num_tiles;
+  const int32_t* idx;     // dense-vector index of each atom
+  const float* val;       // values
+  const int32_t* perm;    // nullable: values gathered through perm
+  const float* vec;       // dense input vector
+  float* out;             // per-tile output
+  int32_t check;          // > 0: validate idx against it
+  int* status;
+  const BatchBases* batch = nullptr;  // x offsets per matrix (batched forward / dvals)
 };
 
 }  // namespace lbh
@@ -72,12 +84,12 @@ struct lb_plan_s {
   lb_schedule_t schedule = LB_MERGE_PATH;
   lb_plan_opts_t opts{};
   int group_size = 32;
-  // single tile set
+  // tile set (single matrix: caller's offsets; batch: plan-owned global offsets)
   const int32_t* rp = nullptr;
   int32_t num_tiles = 0;
   int32_t num_cols = 0;
   int64_t num_atoms = 0;
-  lbh::MpTable mp;        // forward merge-path table (schedule or dvals / atom_tiles)
+  lbh::MpTable mp;        // forward merge-path table (schedule, dvals, atom tiles)
   // transpose (backward)
   bool has_t = false;
   int32_t t_cols = 0;
@@ -86,35 +98,23 @@ struct lb_plan_s {
   int32_t* perm = nullptr;
   lbh::MpTable mp_t;
   // batch
-  lbh::BatchSet bs, bs_t;
-  int32_t* perm_t_local = nullptr;
-  int32_t* riT_local = nullptr;
-  int32_t* cp_cat_t = nullptr;
+  int32_t* rp_global = nullptr;  // owned global row offsets
+  lbh::BatchBases bb;
   // device error word
   int* d_status = nullptr;
 };
 
 namespace lbh {
 
-// merge-path table construction and launches (lb_merge.cu)
-lb_status_t build_mp_table_single(MpTable& t, const int32_t* rp, int32_t R, int64_t N, int ipt, int num_sms,
-                                  int ctas_per_sm, cudaStream_t s);
-lb_status_t build_mp_table_batch(MpTable& t, const BatchSet& b, int ipt, int num_sms, int ctas_per_sm,
-                                 cudaStream_t s);
-// y = A x over the table's tile set; idx/val/perm/vec/out as in lbk::AtomView.
-lb_status_t launch_mp_spmv(const MpTable& t, const int32_t* rp, const BatchSet* b, const int32_t* idx,
-                           const float* val, const int32_t* perm, const float* vec, float* out, int64_t num_tiles,
-                           int32_t check_cols, int* status, cudaStream_t s);
+// merge-path tables and launches (lb_merge.cu)
+lb_status_t build_mp_table(MpTable& t, const int32_t* rp, int32_t R, int64_t N, int ipt, int variant, int num_sms,
+                           int ctas_per_sm, const BatchBases* batch, cudaStream_t s);
+lb_status_t launch_mp_spmv(const MpTable& t, const SpmvCall& c, cudaStream_t s);
 // dvals[j] = dy[row(j)] * x[idx[j]] (dvals != null) or tile_of_atom[j] = row(j)
-lb_status_t launch_mp_expand(const MpTable& t, const int32_t* rp, const BatchSet* b, const int32_t* idx,
-                             const float* x, const float* dy, float* dvals, int32_t* tile_of_atom,
-                             int32_t check_cols, int* status, cudaStream_t s);
-lb_status_t launch_tm_spmv(const int32_t* rp, int32_t R, const int32_t* idx, const float* val, const int32_t* perm,
-                           const float* vec, float* out, int32_t check_cols, int* status, int num_sms,
-                           cudaStream_t s);
-lb_status_t launch_gm_spmv(int group, const int32_t* rp, int32_t R, const int32_t* idx, const float* val,
-                           const int32_t* perm, const float* vec, float* out, int32_t check_cols, int* status,
-                           int num_sms, cudaStream_t s);
+lb_status_t launch_mp_expand(const MpTable& t, const SpmvCall& c, const float* dy, float* dvals,
+                             int32_t* tile_of_atom, cudaStream_t s);
+lb_status_t launch_tm_spmv(const SpmvCall& c, cudaStream_t s);
+lb_status_t launch_gm_spmv(int group, const SpmvCall& c, int num_sms, cudaStream_t s);
 
 // transpose (lb_transpose.cu): stable counting sort of atoms by key.
 // keys[N] in [0, C); row_of[N]; outputs cp[C+1], riT[N], perm[N].
@@ -127,6 +127,7 @@ lb_status_t device_scan(const int32_t* in, int32_t* out, int64_t n, bool inclusi
 int device_sms(int device);
 int64_t mp_diagonal(int64_t items, int grid, int tiles_per_cta, int items_per_tile, int64_t e);
 void mp_geometry(int64_t items, int grid_cap, int items_per_tile, int block, int* grid, int* tiles_per_cta);
-int occupancy_mp(int ipt, bool batch);
+int occupancy_mp(int ipt, int variant);
+lb_status_t check_columns(const int32_t* ci, int64_t n, int32_t C, cudaStream_t s);
 
 }  // namespace lbh

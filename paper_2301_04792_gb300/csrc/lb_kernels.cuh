@@ -6,6 +6,11 @@
 // merge-path.  Everything here is deterministic: the order in which partial
 // sums are combined depends only on the plan, never on timing, and no
 // floating-point atomics are used.
+//
+// A batch of matrices is run as one block-diagonal tile set: its row offsets
+// are made global once at plan time, and each atom's dense-vector entry is
+// offset by the first column of its matrix (found from the split table's
+// per-split matrix index).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -16,7 +21,10 @@
 namespace lbk {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kDevErrColumn = 1;  // device error bit: column index out of range
+constexpr int kDevErrColumn = 1;   // device error bit: column index out of range
+constexpr int kDevErrTimeout = 2;  // device error bit: a bounded wait gave up
+constexpr int kStages = 3;         // shared-memory ring depth of the merge-path pipeline
+constexpr long long kSpinLimit = 1LL << 26;
 
 // ------------------------------------------------------------- load helpers --
 
@@ -30,9 +38,8 @@ __device__ __forceinline__ float4 ld_stream(const float4* p) { return __ldcs(p);
 // How atom j of a tile set becomes a product.  idx[j] selects the entry of the
 // dense vector (a column for y = A x, a row for dx = A^T dy); the value is
 // val[j], or val[perm[j]] when the tile set is a transpose that gathers the
-// original values.  `vbase` offsets perm for batched transposes (perm is
-// matrix-local there).  With check > 0 every index is checked against it;
-// an out-of-range index reads as 0 and sets a bit in *status.
+// original values.  With check > 0 every index is checked against it; an
+// out-of-range index reads as 0 and sets a bit in *status.
 struct AtomView {
   const int32_t* idx;
   const float* val;
@@ -41,19 +48,19 @@ struct AtomView {
   int32_t check;
   int* status;
 
-  __device__ __forceinline__ float value(int64_t j, int64_t vbase) const {
-    return perm ? __ldg(val + vbase + ld_stream(perm + j)) : ld_stream(val + j);
+  __device__ __forceinline__ float value(int64_t j) const {
+    return perm ? __ldg(val + ld_stream(perm + j)) : ld_stream(val + j);
   }
   __device__ __forceinline__ float gather(int c, int64_t xbase) const {
     if (check > 0 && (unsigned)c >= (unsigned)check) {
-      atomicOr(status, kDevErrColumn);
+      if (status) atomicOr(status, kDevErrColumn);
       return 0.f;
     }
     return __ldg(vec + xbase + c);
   }
-  __device__ __forceinline__ float product(int64_t j, int64_t vbase, int64_t xbase) const {
+  __device__ __forceinline__ float product(int64_t j, int64_t xbase) const {
     const int c = ld_stream(idx + j);
-    return value(j, vbase) * gather(c, xbase);
+    return value(j) * gather(c, xbase);
   }
 };
 
@@ -107,51 +114,85 @@ __device__ __forceinline__ int group_excl_scan_small(int x, int lane_in_group, i
   return incl - x;
 }
 
+// ------------------------------------------------------ mbarrier and TMA --
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for a phase of `bar`: gives up after kSpinLimit polls and
+// returns false (the caller records kDevErrTimeout and winds down).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (long long n = 0; n < kSpinLimit; ++n)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// 1-D bulk copy (TMA) global -> shared, completion counted on `bar`.
+// dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // ------------------------------------------------------------ merge path --
 
-// One split of the merged list of row ends and atoms: i row ends and j atoms
-// precede it; m is the matrix it falls in (batched tile sets only).
-struct Split64 {
-  int64_t i, j;
-  int32_t m, pad;
-};
-
 // Arguments of the merge-path kernels.  `splits` holds, for every persistent
-// CTA c, tiles_per_cta + 1 consecutive splits (its tile boundaries).
+// CTA c, tiles_per_cta + 1 consecutive (row, atom) splits: the boundaries of
+// its tiles, each on the diagonal given by the plan.
 struct MpArgs {
-  const int32_t* rp;        // single: tile offsets; batch: per-matrix offsets back to back
-  const int64_t* row_base;  // batch: first global tile of each matrix [M+1]
-  const int64_t* nnz_base;  // batch: first global atom of each matrix [M+1]
-  const int64_t* vec_base;  // batch: first entry of each matrix's dense input vector [M+1]
+  const int32_t* rp;        // row offsets [num_tiles + 1] (global ones for a batch)
   AtomView atoms;
   float* out;               // per-tile result (y or dx)
-  const void* splits;       // int2 (single) or Split64 (batch)
+  const int2* splits;
+  const int32_t* split_m;   // batch: matrix of every split's atom (nullptr otherwise)
+  const int64_t* nnz_base;  // batch: first atom of each matrix
+  const int64_t* vec_base;  // batch: first dense-vector entry of each matrix
   int tiles_per_cta;
   int num_ctas;
-  int64_t num_tiles;
+  int items_per_tile;
+  int32_t num_tiles;
   float* carry_val;         // [num_ctas]
-  int64_t* carry_row;       // [num_ctas]
+  int32_t* carry_row;       // [num_ctas]
   unsigned* ticket;         // zero between launches
+  int* status;
   // expand kernels
   const float* dy;          // dvals: upstream gradient per tile
   float* dvals;             // dvals output per atom
   int32_t* tile_of_atom;    // atom -> tile output
 };
-
-template <bool BATCH>
-__device__ __forceinline__ Split64 load_split(const MpArgs& a, size_t e) {
-  if constexpr (BATCH) {
-    return reinterpret_cast<const Split64*>(a.splits)[e];
-  } else {
-    const int2 s = __ldg(reinterpret_cast<const int2*>(a.splits) + e);
-    Split64 r;
-    r.i = s.x;
-    r.j = s.y;
-    r.m = 0;
-    r.pad = 0;
-    return r;
-  }
-}
 
 // Largest m in [lo, hi] with base[m] <= g (the matrix holding global index g).
 __device__ __forceinline__ int find_matrix(const int64_t* base, int lo, int hi, int64_t g) {
@@ -163,181 +204,398 @@ __device__ __forceinline__ int find_matrix(const int64_t* base, int lo, int hi, 
   return lo;
 }
 
-// Row ends of the tile's rows, relative to its first atom, into s_end[0..nrows).
-template <int BLOCK, bool BATCH>
-__device__ __forceinline__ void stage_row_ends(const MpArgs& a, const Split64& cur, const Split64& nxt, int nrows,
-                                               int* s_end) {
-  if constexpr (!BATCH) {
-    const int32_t* rp = a.rp + cur.i + 1;
-    const int j0 = (int)cur.j;
-    for (int r = threadIdx.x; r < nrows; r += BLOCK) s_end[r] = __ldg(rp + r) - j0;
+// Dense-vector offset of atom j of a tile whose atoms lie in matrices [m0, m1].
+template <bool XB>
+__device__ __forceinline__ int64_t atom_xbase(const MpArgs& a, int m0, int m1, int64_t xb0, int64_t j) {
+  if constexpr (!XB) {
+    return 0;
   } else {
-    for (int r = threadIdx.x; r < nrows; r += BLOCK) {
-      const int64_t g = cur.i + r;
-      const int m = (cur.m == nxt.m) ? cur.m : find_matrix(a.row_base, cur.m, nxt.m, g);
-      const int64_t end = __ldg(a.nnz_base + m) + __ldg(a.rp + g + m + 1);
-      s_end[r] = (int)(end - cur.j);
-    }
-  }
-}
-
-// Products of the tile's atoms into s_prod[off + l], l in [0, nnz), with
-// off = (first atom) & 3 so that 16-byte vectors of col_idx / vals land on
-// 16-byte shared-memory boundaries.  VEC: col_idx, vals (or perm) 16-byte aligned.
-template <int BLOCK, int IPT, bool BATCH, bool VEC>
-__device__ __forceinline__ void stage_products(const MpArgs& a, const Split64& cur, const Split64& nxt, int nnz,
-                                               float* s_prod) {
-  const int64_t j0 = cur.j;
-  const int off = (int)(j0 & 3);
-  const AtomView& at = a.atoms;
-  int m_uni = 0;
-  int64_t vb = 0, xb = 0;
-  const bool uniform = !BATCH || cur.m == nxt.m;
-  if constexpr (BATCH) {
-    m_uni = cur.m;
-    vb = __ldg(a.nnz_base + m_uni);
-    xb = __ldg(a.vec_base + m_uni);
-  }
-  if constexpr (VEC) {
-    const int64_t g0 = j0 - off;  // multiple of 4
-    const int nv = (off + nnz) >> 2;
-    constexpr int NV = (BLOCK * IPT + 4) / 4 / BLOCK + 1;
-    const int4* idx4 = reinterpret_cast<const int4*>(at.idx + g0);
-    if (uniform && at.perm == nullptr) {
-      const float4* val4 = reinterpret_cast<const float4*>(at.val + g0);
-      int4 c[NV];
-      float4 w[NV];
-#pragma unroll
-      for (int u = 0; u < NV; ++u) {
-        const int q = threadIdx.x + u * BLOCK;
-        if (q < nv) {
-          c[u] = ld_stream(idx4 + q);
-          w[u] = ld_stream(val4 + q);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < NV; ++u) {
-        const int q = threadIdx.x + u * BLOCK;
-        if (q < nv) {
-          // slots below `off` belong to atoms before the tile; in a batch they may
-          // belong to another matrix, so they are not gathered
-          const int s0 = 4 * q;
-          float4 p;
-          p.x = (BATCH && s0 + 0 < off) ? 0.f : w[u].x * at.gather(c[u].x, xb);
-          p.y = (BATCH && s0 + 1 < off) ? 0.f : w[u].y * at.gather(c[u].y, xb);
-          p.z = (BATCH && s0 + 2 < off) ? 0.f : w[u].z * at.gather(c[u].z, xb);
-          p.w = w[u].w * at.gather(c[u].w, xb);
-          *reinterpret_cast<float4*>(s_prod + s0) = p;
-        }
-      }
-    } else if (uniform) {
-      const int4* perm4 = reinterpret_cast<const int4*>(at.perm + g0);
-      int4 c[NV], pm[NV];
-#pragma unroll
-      for (int u = 0; u < NV; ++u) {
-        const int q = threadIdx.x + u * BLOCK;
-        if (q < nv) {
-          c[u] = ld_stream(idx4 + q);
-          pm[u] = ld_stream(perm4 + q);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < NV; ++u) {
-        const int q = threadIdx.x + u * BLOCK;
-        if (q < nv) {
-          const int s0 = 4 * q;
-          float4 p;
-          p.x = (BATCH && s0 + 0 < off) ? 0.f : __ldg(at.val + vb + pm[u].x) * at.gather(c[u].x, xb);
-          p.y = (BATCH && s0 + 1 < off) ? 0.f : __ldg(at.val + vb + pm[u].y) * at.gather(c[u].y, xb);
-          p.z = (BATCH && s0 + 2 < off) ? 0.f : __ldg(at.val + vb + pm[u].z) * at.gather(c[u].z, xb);
-          p.w = __ldg(at.val + vb + pm[u].w) * at.gather(c[u].w, xb);
-          *reinterpret_cast<float4*>(s_prod + s0) = p;
-        }
-      }
-    } else {
-      // tile spans several matrices (batch): per-atom matrix lookup, scalar loads
-      for (int l = threadIdx.x; l < nnz; l += BLOCK) {
-        const int64_t j = j0 + l;
-        const int m = find_matrix(a.nnz_base, cur.m, nxt.m, j);
-        s_prod[off + l] = at.product(j, __ldg(a.nnz_base + m), __ldg(a.vec_base + m));
-      }
-      return;
-    }
-    // ragged tail past the last full vector
-    const int tail0 = 4 * nv > off ? 4 * nv : off;
-    for (int l = tail0 + threadIdx.x; l < off + nnz; l += BLOCK) {
-      s_prod[l] = at.product(g0 + l, vb, xb);
-    }
-  } else {
-    for (int l = threadIdx.x; l < nnz; l += BLOCK) {
-      const int64_t j = j0 + l;
-      int64_t vbj = vb, xbj = xb;
-      if (!uniform) {
-        const int m = find_matrix(a.nnz_base, cur.m, nxt.m, j);
-        vbj = __ldg(a.nnz_base + m);
-        xbj = __ldg(a.vec_base + m);
-      }
-      s_prod[off + l] = at.product(j, vbj, xbj);
-    }
+    if (m0 == m1) return xb0;
+    return __ldg(a.vec_base + find_matrix(a.nnz_base, m0, m1, j));
   }
 }
 
 // Split of local diagonal d inside a tile: smallest ti with
-// ti == min(d, nrows) or s_end[ti] > d - ti - 1 (row end ti comes after atom
-// d - ti - 1; a row end precedes the atom with the same index).
-__device__ __forceinline__ int tile_search(const int* s_end, int d, int nrows, int nnz) {
+// ti == min(d, nrows) or end(ti) > d - ti - 1 (row end ti comes after atom
+// d - ti - 1; a row end precedes the atom with the same index), where end(r)
+// is the row end relative to the tile's first atom.
+template <class End>
+__device__ __forceinline__ int tile_search(End end, int d, int nrows, int nnz) {
   int lo = d - nnz > 0 ? d - nnz : 0;
   int hi = d < nrows ? d : nrows;
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
-    if (s_end[mid] > d - mid - 1) hi = mid;
+    if (end(mid) > d - mid - 1) hi = mid;
     else lo = mid + 1;
   }
   return lo;
 }
 
-template <int BLOCK, int IPT>
-constexpr size_t mp_smem_bytes() {
-  return sizeof(int) * (BLOCK * IPT) + sizeof(float) * (BLOCK * IPT + 4) + sizeof(float) * (BLOCK * IPT) + 64;
+// Fix-up of rows split between CTAs, run by the last CTA to finish: y[row] +=
+// the carries of all CTAs that left `row` open, combined in CTA order by a
+// segmented scan keyed by row.  Resets the ticket for the next launch.
+template <int BLOCK>
+__device__ __forceinline__ void last_cta_fixup(const MpArgs& a, float* s_wv, int* s_wf, float* s_incl) {
+  float run = 0.f;
+  for (int b = 0; b < a.num_ctas; b += BLOCK) {
+    const int e = b + threadIdx.x;
+    const bool valid = e < a.num_ctas;
+    const int row = valid ? __ldcg(a.carry_row + e) : -2;
+    const float val = valid ? __ldcg(a.carry_val + e) : 0.f;
+    const int prev = (e == 0) ? -3 : (valid ? __ldcg(a.carry_row + e - 1) : -2);
+    const int next = (e + 1 < a.num_ctas) ? __ldcg(a.carry_row + e + 1) : -4;
+    float excl, total;
+    const float incl = block_seg_scan<BLOCK>(val, row != prev, run, s_wv, s_wf, s_incl, excl, total);
+    if (valid && row >= 0 && row != next) {
+      float* py = a.out + row;
+      __stcg(py, __ldcg(py) + incl);
+    }
+    run = total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *a.ticket = 0u;
 }
 
-// Merge-path SpMV (Sec. 5.2.1) as a persistent kernel: CTA c owns an equal
-// share of rows + atoms and walks it tile by tile.  Per tile: stage row ends
-// and atom products in shared memory, split the tile evenly over the threads
-// by a search along each thread's diagonal, walk IPT items per thread
-// (complete rows are written directly; the partial row at each thread's end is
-// its carry-out), resolve carries across threads with a segmented scan and
-// across tiles with a running CTA carry.  Rows split between CTAs are fixed up
-// by the last CTA to finish (ticket), in CTA order.
-template <int BLOCK, int IPT, bool BATCH, bool VEC>
-__global__ void __launch_bounds__(BLOCK) mp_spmv_kernel(MpArgs a) {
+// Carry-out of a CTA and the ticket that elects the last CTA.  Returns true in
+// the last CTA (all threads).
+template <int BLOCK>
+__device__ __forceinline__ bool publish_carry(const MpArgs& a, int32_t open_row, float carry, int* s_last) {
+  if (threadIdx.x == 0) {
+    a.carry_row[blockIdx.x] = open_row < a.num_tiles ? open_row : -1;
+    a.carry_val[blockIdx.x] = carry;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) *s_last = (atomicAdd(a.ticket, 1u) == (unsigned)(a.num_ctas - 1));
+  __syncthreads();
+  const bool last = *s_last != 0;
+  if (last) __threadfence();
+  return last;
+}
+
+// Shared-memory layout of the pipelined merge-path kernel: kStages ring slots,
+// each holding the tile's window of atom indices, of values (or perm), and of
+// row offsets, each W = T + 8 words (the window starts at the 16-byte boundary
+// at or below the tile's first element); then per-tile scratch: the row whose
+// last atom sits in each slot, one bit per slot marking those row ends, and the
+// tile's row results.
+template <int BLOCK, int IPT>
+struct MpLayout {
+  static constexpr int T = BLOCK * IPT;
+  static constexpr int W = T + 8;
+  static constexpr int NBW = (W + 31) / 32;
+  static constexpr size_t stage_words = 3 * (size_t)W;
+  static constexpr size_t bytes = sizeof(int) * (kStages * stage_words + W + NBW + T);
+};
+
+template <int BLOCK, int IPT>
+constexpr size_t mp_smem_bytes() {
+  return MpLayout<BLOCK, IPT>::bytes;
+}
+
+// Merge-path SpMV (Sec. 5.2.1) as a persistent, pipelined kernel.  CTA c owns
+// an equal share of rows + atoms (the setup step: the plan's split table cuts
+// it into tiles of T = BLOCK * IPT merge items, each split found by the search
+// along its diagonal).  Within a tile the T items are again split evenly over
+// the threads, in two passes instead of one interleaved walk: every thread
+// takes at most IPT of the tile's rows (marking where each non-empty row ends)
+// and at most IPT of its atoms (accumulating products and closing a row at
+// each mark), so no thread holds more than about IPT + 1 items.  Per tile:
+//   1. one thread streams the tile's atom indices, values (or perm) and row
+//      offsets into a ring slot with 1-D bulk copies (TMA), two tiles ahead;
+//   2. one tile ahead, every thread issues the dense-vector gathers of its
+//      atoms into registers;
+//   3. row pass: empty rows get 0, a row that closes at the tile's start gets
+//      the running carry, every other row marks the slot of its last atom;
+//   4. atom pass: products are summed per thread in atom order, a mark closes
+//      the row; a block segmented scan in thread order resolves rows that
+//      cross threads (with the CTA's running carry in front);
+//   5. the tile's rows are stored coalesced.
+// Rows split between CTAs are fixed up by the last CTA to finish.
+// Requires 16-byte aligned idx, val/perm and rp.
+template <int BLOCK, int IPT, bool XB, bool PERM>
+__global__ void __launch_bounds__(BLOCK) mp_spmv_tma_kernel(MpArgs a) {
+  static_assert(IPT % 4 == 0 && 32 % IPT == 0, "IPT must be 4, 8 or 16");
+  using L = MpLayout<BLOCK, IPT>;
+  constexpr int T = L::T;
+  constexpr int W = L::W;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  int* s_ring = reinterpret_cast<int*>(smem_raw);
+  int* s_endrow = s_ring + kStages * L::stage_words;       // W
+  unsigned* s_bits = reinterpret_cast<unsigned*>(s_endrow + W);  // NBW
+  float* s_y = reinterpret_cast<float*>(s_bits + L::NBW);  // T
+  __shared__ __align__(8) uint64_t s_bar[kStages];
+  __shared__ float s_wv[BLOCK / 32];
+  __shared__ int s_wf[BLOCK / 32];
+  __shared__ float s_incl[BLOCK];
+  __shared__ int s_last;
+  __shared__ int s_abort;
+
+  const int tid = threadIdx.x;
+  const int2* sp = a.splits + (size_t)blockIdx.x * (a.tiles_per_cta + 1);
+  const int32_t* sm = XB ? a.split_m + (size_t)blockIdx.x * (a.tiles_per_cta + 1) : nullptr;
+  const AtomView& at = a.atoms;
+
+  // number of non-empty tiles of this CTA (tiles hold a.items_per_tile <= T - 4 items)
+  int ntiles = 0;
+  {
+    const int2 e0 = __ldg(sp);
+    const int2 e1 = __ldg(sp + a.tiles_per_cta);
+    const int64_t share = (int64_t)(e1.x - e0.x) + (e1.y - e0.y);
+    ntiles = (int)((share + a.items_per_tile - 1) / a.items_per_tile);
+  }
+
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&s_bar[s], 1);
+    fence_mbar_init();
+    s_abort = 0;
+  }
+  for (int w = tid; w < L::NBW; w += BLOCK) s_bits[w] = 0u;
+  __syncthreads();
+
+  auto idx_slot = [&](int s) { return s_ring + (size_t)s * L::stage_words; };
+  auto val_slot = [&](int s) { return s_ring + (size_t)s * L::stage_words + W; };
+  auto rp_slot = [&](int s) { return s_ring + (size_t)s * L::stage_words + 2 * W; };
+
+  // Stream tile t into its ring slot: bulk copies of the 16-byte aligned body,
+  // plain loads of the (at most 3-element) ragged ends.
+  auto issue = [&](int t) {
+    const int s = t % kStages;
+    const int2 c0 = __ldg(sp + t), c1 = __ldg(sp + t + 1);
+    const int a_lo = c0.y & ~3, a_hi = c1.y & ~3;
+    const int p_lo = (c0.x + 1) & ~3, p_hi = (c1.x + 1) & ~3;
+    const int32_t* vsrc = PERM ? at.perm : reinterpret_cast<const int32_t*>(at.val);
+    if (tid == 0) {
+      const uint32_t ab = a_hi > a_lo ? (uint32_t)(a_hi - a_lo) * 4u : 0u;
+      const uint32_t pb = p_hi > p_lo ? (uint32_t)(p_hi - p_lo) * 4u : 0u;
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&s_bar[s], 2 * ab + pb);
+      if (ab) {
+        tma_load_1d(idx_slot(s), at.idx + a_lo, ab, &s_bar[s]);
+        tma_load_1d(val_slot(s), vsrc + a_lo, ab, &s_bar[s]);
+      }
+      if (pb) tma_load_1d(rp_slot(s), a.rp + p_lo, pb, &s_bar[s]);
+    } else if (tid >= 32 && tid < 35) {
+      const int j = (a_hi > c0.y ? a_hi : c0.y) + (tid - 32);
+      if (j < c1.y) {
+        idx_slot(s)[j - a_lo] = __ldg(at.idx + j);
+        val_slot(s)[j - a_lo] = __ldg(vsrc + j);
+      }
+    } else if (tid >= 64 && tid < 67) {
+      const int q = (p_hi > c0.x + 1 ? p_hi : c0.x + 1) + (tid - 64);
+      if (q < c1.x + 1) rp_slot(s)[q - p_lo] = __ldg(a.rp + q);
+    }
+  };
+
+  // gathers of this thread's atoms of one tile, issued a tile ahead
+  struct Gath {
+    float xg[IPT];
+    float vg[PERM ? IPT : 1];
+  };
+  auto clear = [&](Gath& g) {
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) {
+      g.xg[q] = 0.f;
+      if constexpr (PERM) g.vg[q] = 0.f;
+    }
+  };
+
+  // returns false if the wait gave up: the slot's contents must then not be used
+  auto wait_tile = [&](int t) -> bool {
+    if (!mbar_wait_bounded(&s_bar[t % kStages], (uint32_t)((t / kStages) & 1))) {
+      atomicOr(&s_abort, 1);
+      if (a.status) atomicOr(a.status, kDevErrTimeout);
+      return false;
+    }
+    return true;
+  };
+
+  auto prefetch = [&](int t, Gath& g) {
+    const int s = t % kStages;
+    const int2 c0 = __ldg(sp + t), c1 = __ldg(sp + t + 1);
+    const int nnz = c1.y - c0.y, off = c0.y & 3, j0 = c0.y;
+    int m0 = 0, m1 = 0;
+    int64_t xb0 = 0;
+    if constexpr (XB) {
+      m0 = __ldg(sm + t);
+      m1 = __ldg(sm + t + 1);
+      xb0 = __ldg(a.vec_base + m0);
+    }
+    const int s0 = tid * IPT;
+    int c[IPT];
+    int pm[PERM ? IPT : 1];
+#pragma unroll
+    for (int q = 0; q < IPT; q += 4) {
+      const int4 c4 = *reinterpret_cast<const int4*>(idx_slot(s) + s0 + q);
+      c[q] = c4.x;
+      c[q + 1] = c4.y;
+      c[q + 2] = c4.z;
+      c[q + 3] = c4.w;
+      if constexpr (PERM) {
+        const int4 p4 = *reinterpret_cast<const int4*>(val_slot(s) + s0 + q);
+        pm[q] = p4.x;
+        pm[q + 1] = p4.y;
+        pm[q + 2] = p4.z;
+        pm[q + 3] = p4.w;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) {
+      const int l = s0 + q - off;
+      g.xg[q] = 0.f;
+      if constexpr (PERM) g.vg[q] = 0.f;
+      if ((unsigned)l < (unsigned)nnz) {
+        g.xg[q] = at.gather(c[q], atom_xbase<XB>(a, m0, m1, xb0, (int64_t)j0 + l));
+        if constexpr (PERM) g.vg[q] = __ldg(at.val + pm[q]);
+      }
+    }
+  };
+
+  float carry = 0.f;
+  int32_t open_row = __ldg(sp).x;
+  int issued = 0;  // tiles [0, issued) have bulk copies issued
+  int waited = 0;  // tiles [0, waited) have been waited for
+  Gath cur, nxt;
+  clear(cur);
+  clear(nxt);
+  if (ntiles > 0) {
+    issue(0);
+    if (ntiles > 1) issue(1);
+    issued = ntiles > 1 ? 2 : 1;
+    __syncthreads();  // plain-loaded ends of tiles 0 and 1 visible
+    if (wait_tile(0)) prefetch(0, cur);
+    waited = 1;
+  }
+  for (int k = 0; k < ntiles; ++k) {
+    if (k + 2 < ntiles) {
+      issue(k + 2);
+      issued = k + 3;
+    }
+    if (k + 1 < ntiles) {
+      if (wait_tile(k + 1)) prefetch(k + 1, nxt);
+      else clear(nxt);
+      waited = k + 2;
+    }
+    const int s = k % kStages;
+    const int2 c0 = __ldg(sp + k), c1 = __ldg(sp + k + 1);
+    const int nrows = c1.x - c0.x, nnz = c1.y - c0.y;
+    const int off = c0.y & 3, roff = (c0.x + 1) & 3, j0 = c0.y;
+    const int* rps = rp_slot(s) + roff;
+
+    // row pass
+    for (int r = tid; r < nrows; r += BLOCK) {
+      const int e = rps[r] - j0;
+      const int pe = r ? rps[r - 1] - j0 : -1;
+      if (r > 0 && e == pe) {
+        s_y[r] = 0.f;  // empty row
+      } else if (e == 0) {
+        s_y[r] = carry;  // first row, closed at the tile's start
+      } else {
+        const int slot = e - 1 + off;
+        s_endrow[slot] = r;
+        atomicOr(&s_bits[slot >> 5], 1u << (slot & 31));
+      }
+    }
+    const float prefix = (nrows > 0 && rps[0] == j0) ? 0.f : carry;
+    __syncthreads();
+
+    // atom pass
+    const int s0 = tid * IPT;
+    const unsigned bits = s_bits[s0 >> 5] >> (s0 & 31);
+    const int* vsl = val_slot(s);
+    float vv[IPT];
+#pragma unroll
+    for (int q = 0; q < IPT; q += 4) {
+      const float4 v4 = *reinterpret_cast<const float4*>(vsl + s0 + q);
+      vv[q] = v4.x;
+      vv[q + 1] = v4.y;
+      vv[q + 2] = v4.z;
+      vv[q + 3] = v4.w;
+    }
+    float acc = 0.f, first = 0.f;
+    int any = 0, first_row = 0;
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) {
+      const int l = s0 + q - off;
+      const float v = PERM ? cur.vg[q] : ((unsigned)l < (unsigned)nnz ? vv[q] : 0.f);
+      acc += v * cur.xg[q];
+      if ((bits >> q) & 1u) {
+        const int r = s_endrow[s0 + q];
+        if (any) {
+          s_y[r] = acc;
+        } else {
+          first = acc;
+          first_row = r;
+          any = 1;
+        }
+        acc = 0.f;
+      }
+    }
+    float excl, total;
+    block_seg_scan<BLOCK>(acc, any, prefix, s_wv, s_wf, s_incl, excl, total);
+    if (any) s_y[first_row] = excl + first;
+    carry = total;
+    __syncthreads();
+    for (int r = tid; r < nrows; r += BLOCK) a.out[c0.x + r] = s_y[r];
+    for (int w = tid; w < L::NBW; w += BLOCK) s_bits[w] = 0u;
+    open_row = c1.x;
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) {
+      cur.xg[q] = nxt.xg[q];
+      if constexpr (PERM) cur.vg[q] = nxt.vg[q];
+    }
+    __syncthreads();  // ring slot k % kStages and the tile scratch free again
+    if (s_abort) break;
+  }
+  if (s_abort && tid == 0) {
+    // wind down: wait (bounded) for this CTA's bulk copies still in flight
+    for (int t = waited > 0 ? waited - 1 : 0; t < issued; ++t)
+      mbar_wait_bounded(&s_bar[t % kStages], (uint32_t)((t / kStages) & 1));
+  }
+  if (!publish_carry<BLOCK>(a, open_row, carry, &s_last)) return;
+  last_cta_fixup<BLOCK>(a, s_wv, s_wf, s_incl);
+}
+
+// Merge-path SpMV without bulk copies, for buffers that are not 16-byte
+// aligned: per tile, row ends and atom products are staged in shared memory
+// with plain loads, then walked as above.
+template <int BLOCK, int IPT, bool XB>
+__global__ void __launch_bounds__(BLOCK) mp_spmv_plain_kernel(MpArgs a) {
   constexpr int T = BLOCK * IPT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* s_prod = reinterpret_cast<float*>(smem_raw);     // T + 4
-  int* s_end = reinterpret_cast<int*>(s_prod + T + 4);    // T
-  float* s_y = reinterpret_cast<float*>(s_end + T);       // T
+  float* s_prod = reinterpret_cast<float*>(smem_raw);  // T
+  int* s_end = reinterpret_cast<int*>(s_prod + T);     // T
+  float* s_y = reinterpret_cast<float*>(s_end + T);    // T
   __shared__ float s_wv[BLOCK / 32];
   __shared__ int s_wf[BLOCK / 32];
   __shared__ float s_incl[BLOCK];
   __shared__ int s_last;
 
   const int tid = threadIdx.x;
-  const size_t base = (size_t)blockIdx.x * (a.tiles_per_cta + 1);
+  const int2* sp = a.splits + (size_t)blockIdx.x * (a.tiles_per_cta + 1);
+  const int32_t* sm = XB ? a.split_m + (size_t)blockIdx.x * (a.tiles_per_cta + 1) : nullptr;
   float carry = 0.f;
-  Split64 cur = load_split<BATCH>(a, base);
+  int2 cur = __ldg(sp);
   for (int k = 0; k < a.tiles_per_cta; ++k) {
-    const Split64 nxt = load_split<BATCH>(a, base + k + 1);
-    const int nrows = (int)(nxt.i - cur.i);
-    const int nnz = (int)(nxt.j - cur.j);
-    const int items = nrows + nnz;
+    const int2 nxt = __ldg(sp + k + 1);
+    const int nrows = nxt.x - cur.x, nnz = nxt.y - cur.y, items = nrows + nnz;
     if (items == 0) break;
-    stage_row_ends<BLOCK, BATCH>(a, cur, nxt, nrows, s_end);
-    stage_products<BLOCK, IPT, BATCH, VEC>(a, cur, nxt, nnz, s_prod);
-    const int off = (int)(cur.j & 3);
+    int m0 = 0, m1 = 0;
+    int64_t xb0 = 0;
+    if constexpr (XB) {
+      m0 = __ldg(sm + k);
+      m1 = __ldg(sm + k + 1);
+      xb0 = __ldg(a.vec_base + m0);
+    }
+    for (int r = tid; r < nrows; r += BLOCK) s_end[r] = __ldg(a.rp + cur.x + 1 + r) - cur.y;
+    for (int l = tid; l < nnz; l += BLOCK) {
+      const int64_t j = (int64_t)cur.y + l;
+      s_prod[l] = a.atoms.product(j, atom_xbase<XB>(a, m0, m1, xb0, j));
+    }
     __syncthreads();
-
+    auto end = [&](int r) { return s_end[r]; };
     const int d = min(tid * IPT, items);
-    int ti = tile_search(s_end, d, nrows, nnz);
+    int ti = tile_search(end, d, nrows, nnz);
     int tj = d - ti;
     const int ti0 = ti;
     const int dend = min(d + IPT, items);
@@ -357,7 +615,7 @@ __global__ void __launch_bounds__(BLOCK) mp_spmv_kernel(MpArgs a) {
           ++ti;
           nend = ti < nrows ? s_end[ti] : INT_MAX;
         } else {
-          acc += s_prod[off + tj];
+          acc += s_prod[tj];
           ++tj;
         }
       }
@@ -367,66 +625,41 @@ __global__ void __launch_bounds__(BLOCK) mp_spmv_kernel(MpArgs a) {
     if (any) s_y[ti0] = excl + first;
     carry = total;
     __syncthreads();
-    for (int r = tid; r < nrows; r += BLOCK) a.out[cur.i + r] = s_y[r];
+    for (int r = tid; r < nrows; r += BLOCK) a.out[cur.x + r] = s_y[r];
     cur = nxt;
   }
+  if (!publish_carry<BLOCK>(a, cur.x, carry, &s_last)) return;
+  last_cta_fixup<BLOCK>(a, s_wv, s_wf, s_incl);
+}
 
-  // carry-out of this CTA: the row left open at the end of its share
-  if (tid == 0) {
-    a.carry_row[blockIdx.x] = cur.i < a.num_tiles ? cur.i : -1;
-    a.carry_val[blockIdx.x] = carry;
-  }
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) s_last = (atomicAdd(a.ticket, 1u) == (unsigned)(a.num_ctas - 1));
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-
-  // Fix-up by the last CTA: y[row] += sum of the carries of all CTAs that left
-  // `row` open, combined in CTA order by a segmented scan keyed by row.
-  float run = 0.f;
-  for (int b = 0; b < a.num_ctas; b += BLOCK) {
-    const int e = b + tid;
-    const bool valid = e < a.num_ctas;
-    const int64_t row = valid ? __ldcg(a.carry_row + e) : -2;
-    const float val = valid ? __ldcg(a.carry_val + e) : 0.f;
-    const int64_t prev = (e == 0) ? -3 : (valid ? __ldcg(a.carry_row + e - 1) : -2);
-    const int64_t next = (e + 1 < a.num_ctas) ? __ldcg(a.carry_row + e + 1) : -4;
-    float excl, total;
-    const float incl = block_seg_scan<BLOCK>(val, row != prev, run, s_wv, s_wf, s_incl, excl, total);
-    if (valid && row >= 0 && row != next) {
-      float* py = a.out + row;
-      __stcg(py, __ldcg(py) + incl);
-    }
-    run = total;
-    __syncthreads();
-  }
-  if (tid == 0) *a.ticket = 0u;
+template <int BLOCK, int IPT>
+constexpr size_t mp_plain_smem_bytes() {
+  return sizeof(float) * 3 * (size_t)(BLOCK * IPT);
 }
 
 // Merge-path expand: the tile of every atom from the same walk (the
 // schedule's get_tile for all atoms at once), then per atom either
-// tile_of_atom[j] = tile or dvals[j] = dy[tile] * x[col[j]].
-template <int BLOCK, int IPT, bool BATCH, bool DVALS>
+// tile_of_atom[j] = tile or dvals[j] = dy[tile] * x[col[j]] (one correctly
+// rounded FP32 product).
+template <int BLOCK, int IPT, bool XB, bool DVALS>
 __global__ void __launch_bounds__(BLOCK) mp_expand_kernel(MpArgs a) {
   constexpr int T = BLOCK * IPT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int* s_end = reinterpret_cast<int*>(smem_raw);  // T
   int* s_row = s_end + T;                          // T
   const int tid = threadIdx.x;
-  const size_t base = (size_t)blockIdx.x * (a.tiles_per_cta + 1);
-  Split64 cur = load_split<BATCH>(a, base);
+  const int2* sp = a.splits + (size_t)blockIdx.x * (a.tiles_per_cta + 1);
+  const int32_t* sm = XB ? a.split_m + (size_t)blockIdx.x * (a.tiles_per_cta + 1) : nullptr;
+  int2 cur = __ldg(sp);
   for (int k = 0; k < a.tiles_per_cta; ++k) {
-    const Split64 nxt = load_split<BATCH>(a, base + k + 1);
-    const int nrows = (int)(nxt.i - cur.i);
-    const int nnz = (int)(nxt.j - cur.j);
-    const int items = nrows + nnz;
+    const int2 nxt = __ldg(sp + k + 1);
+    const int nrows = nxt.x - cur.x, nnz = nxt.y - cur.y, items = nrows + nnz;
     if (items == 0) break;
-    stage_row_ends<BLOCK, BATCH>(a, cur, nxt, nrows, s_end);
+    for (int r = tid; r < nrows; r += BLOCK) s_end[r] = __ldg(a.rp + cur.x + 1 + r) - cur.y;
     __syncthreads();
+    auto end = [&](int r) { return s_end[r]; };
     const int d = min(tid * IPT, items);
-    int ti = tile_search(s_end, d, nrows, nnz);
+    int ti = tile_search(end, d, nrows, nnz);
     int tj = d - ti;
     const int dend = min(d + IPT, items);
     int nend = ti < nrows ? s_end[ti] : INT_MAX;
@@ -443,20 +676,22 @@ __global__ void __launch_bounds__(BLOCK) mp_expand_kernel(MpArgs a) {
       }
     }
     __syncthreads();
+    int m0 = 0, m1 = 0;
+    int64_t xb0 = 0;
+    if constexpr (XB && DVALS) {
+      m0 = __ldg(sm + k);
+      m1 = __ldg(sm + k + 1);
+      xb0 = __ldg(a.vec_base + m0);
+    }
     for (int l = tid; l < nnz; l += BLOCK) {
-      const int64_t j = cur.j + l;
-      const int64_t row = cur.i + s_row[l];
+      const int64_t j = (int64_t)cur.y + l;
+      const int row = cur.x + s_row[l];
       if constexpr (DVALS) {
-        int64_t xb = 0, yb = 0;
-        if constexpr (BATCH) {
-          const int m = (cur.m == nxt.m) ? cur.m : find_matrix(a.nnz_base, cur.m, nxt.m, j);
-          xb = __ldg(a.vec_base + m);
-          (void)yb;
-        }
         const int c = ld_stream(a.atoms.idx + j);
-        __stcs(a.dvals + j, __fmul_rn(__ldg(a.dy + row), a.atoms.gather(c, xb)));
+        __stcs(a.dvals + j,
+               __fmul_rn(__ldg(a.dy + row), a.atoms.gather(c, atom_xbase<XB>(a, m0, m1, xb0, j))));
       } else {
-        a.tile_of_atom[j] = (int32_t)row;
+        a.tile_of_atom[j] = row;
       }
     }
     __syncthreads();
@@ -480,7 +715,7 @@ __global__ void __launch_bounds__(BLOCK) tm_spmv_kernel(const int32_t* __restric
     for (int k0 = b; k0 < e; k0 += CHUNK) {
       const int k1 = min(e, k0 + CHUNK);
       float part = 0.f;
-      for (int k = k0; k < k1; ++k) part += at.product(k, 0, 0);
+      for (int k = k0; k < k1; ++k) part += at.product(k, 0);
       total += part;
     }
     out[t] = total;
@@ -563,7 +798,7 @@ __global__ void __launch_bounds__(BLOCK) gm_spmv_kernel(const int32_t* __restric
           else hi = mid - 1;
         }
         tile = lo;
-        p = at.product(abase + aa, 0, 0);
+        p = at.product(abase + aa, 0);
       }
       float v = p;
 #pragma unroll

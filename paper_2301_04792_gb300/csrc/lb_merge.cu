@@ -1,7 +1,6 @@
-// Merge-path tables and kernel launches for single and batched tile sets,
-// plus the thread-mapped and group-mapped launchers.
+// Merge-path split tables and kernel launches, plus the thread-mapped and
+// group-mapped launchers.
 #include <algorithm>
-#include <vector>
 
 #include "lb_internal.h"
 #include "lb_kernels.cuh"
@@ -11,25 +10,23 @@ namespace lbh {
 void MpTable::release() {
   cudaFree(splits);
   cudaFree(d_diag);
+  cudaFree(split_m);
   cudaFree(carry_val);
   cudaFree(carry_row);
   cudaFree(ticket);
   splits = nullptr;
   d_diag = nullptr;
+  split_m = nullptr;
   carry_val = nullptr;
   carry_row = nullptr;
   ticket = nullptr;
   built = false;
 }
 
-void BatchSet::release() {
-  if (owns_rp) cudaFree(const_cast<int32_t*>(rp_cat));
-  cudaFree(row_base);
+void BatchBases::release() {
   cudaFree(nnz_base);
   cudaFree(vec_base);
-  cudaFree(diag_base);
-  rp_cat = nullptr;
-  row_base = nnz_base = vec_base = diag_base = nullptr;
+  nnz_base = vec_base = nullptr;
 }
 
 int device_sms(int device) {
@@ -64,44 +61,94 @@ void mp_geometry(int64_t items, int grid_cap, int items_per_tile, int block, int
   *tiles_per_cta = (int)tpc;
 }
 
-template <int IPT, bool BATCH, bool VEC>
-static cudaError_t set_mp_smem() {
-  return cudaFuncSetAttribute(lbk::mp_spmv_kernel<kBlock, IPT, BATCH, VEC>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)lbk::mp_smem_bytes<kBlock, IPT>());
+// ------------------------------------------------------------ instantiations --
+
+template <int IPT, bool XB, bool PERM>
+static void* tma_fn() {
+  return reinterpret_cast<void*>(lbk::mp_spmv_tma_kernel<kBlock, IPT, XB, PERM>);
+}
+template <int IPT, bool XB>
+static void* plain_fn() {
+  return reinterpret_cast<void*>(lbk::mp_spmv_plain_kernel<kBlock, IPT, XB>);
+}
+template <int IPT, bool XB, bool DV>
+static void* expand_fn() {
+  return reinterpret_cast<void*>(lbk::mp_expand_kernel<kBlock, IPT, XB, DV>);
 }
 
-int occupancy_mp(int ipt, bool batch) {
-  int occ = 0;
-  cudaError_t e = cudaSuccess;
-#define OCC_CASE(I)                                                                                   \
-  case I:                                                                                             \
-    if (batch) {                                                                                      \
-      set_mp_smem<I, true, true>();                                                                   \
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lbk::mp_spmv_kernel<kBlock, I, true, true>, \
-                                                        kBlock, lbk::mp_smem_bytes<kBlock, I>());     \
-    } else {                                                                                          \
-      set_mp_smem<I, false, true>();                                                                  \
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lbk::mp_spmv_kernel<kBlock, I, false, true>, \
-                                                        kBlock, lbk::mp_smem_bytes<kBlock, I>());     \
-    }                                                                                                 \
-    break;
+template <int IPT>
+static void* pick_tma(bool xb, bool perm) {
+  if (xb) return perm ? tma_fn<IPT, true, true>() : tma_fn<IPT, true, false>();
+  return perm ? tma_fn<IPT, false, true>() : tma_fn<IPT, false, false>();
+}
+template <int IPT>
+static void* pick_plain(bool xb) {
+  return xb ? plain_fn<IPT, true>() : plain_fn<IPT, false>();
+}
+template <int IPT>
+static void* pick_expand(bool xb, bool dv) {
+  if (xb) return dv ? expand_fn<IPT, true, true>() : expand_fn<IPT, true, false>();
+  return dv ? expand_fn<IPT, false, true>() : expand_fn<IPT, false, false>();
+}
+
+static size_t tma_smem(int ipt) {
   switch (ipt) {
-    OCC_CASE(4)
-    OCC_CASE(8)
-    OCC_CASE(16)
-    default:
-      break;
+    case 4: return lbk::mp_smem_bytes<kBlock, 4>();
+    case 8: return lbk::mp_smem_bytes<kBlock, 8>();
+    default: return lbk::mp_smem_bytes<kBlock, 16>();
   }
-#undef OCC_CASE
-  if (e != cudaSuccess || occ < 1) occ = 1;
+}
+static size_t plain_smem(int ipt) { return sizeof(float) * 3 * (size_t)kBlock * ipt; }
+static size_t expand_smem(int ipt) { return sizeof(int) * 2 * (size_t)kBlock * ipt; }
+
+static void* kernel_tma(int ipt, bool xb, bool perm) {
+  switch (ipt) {
+    case 4: return pick_tma<4>(xb, perm);
+    case 8: return pick_tma<8>(xb, perm);
+    case 16: return pick_tma<16>(xb, perm);
+  }
+  return nullptr;
+}
+static void* kernel_plain(int ipt, bool xb) {
+  switch (ipt) {
+    case 4: return pick_plain<4>(xb);
+    case 8: return pick_plain<8>(xb);
+    case 16: return pick_plain<16>(xb);
+  }
+  return nullptr;
+}
+static void* kernel_expand(int ipt, bool xb, bool dv) {
+  switch (ipt) {
+    case 4: return pick_expand<4>(xb, dv);
+    case 8: return pick_expand<8>(xb, dv);
+    case 16: return pick_expand<16>(xb, dv);
+  }
+  return nullptr;
+}
+
+// Every launch sets the dynamic shared-memory limit of its kernel first (cheap,
+// and correct whichever device is current).
+static cudaError_t launch(void* fn, int grid, size_t smem, cudaStream_t s, lbk::MpArgs* a) {
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  void* args[] = {a};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(kBlock), args, smem, s);
+}
+
+int occupancy_mp(int ipt, int variant) {
+  void* fn = variant == 1 ? kernel_plain(ipt, false) : kernel_tma(ipt, false, false);
+  if (!fn) return 1;
+  const size_t smem = variant == 1 ? plain_smem(ipt) : tma_smem(ipt);
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kBlock, smem) != cudaSuccess || occ < 1) occ = 1;
   return occ;
 }
 
 // ------------------------------------------------------------ split kernels --
 
-__global__ void mp_splits_single_kernel(const int32_t* __restrict__ rp, int32_t R, int64_t N, int64_t items, int grid,
-                                        int tpc, int ipt_items, int64_t entries, int2* out, int64_t* diag) {
+__global__ void mp_splits_kernel(const int32_t* __restrict__ rp, int32_t R, int64_t N, int64_t items, int grid,
+                                 int tpc, int ipt_items, int64_t entries, int2* out, int64_t* diag) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= entries) return;
   const int64_t d = mp_diag(items, grid, tpc, ipt_items, e);
@@ -117,242 +164,149 @@ __global__ void mp_splits_single_kernel(const int32_t* __restrict__ rp, int32_t 
   diag[e] = d;
 }
 
-__global__ void mp_splits_batch_kernel(const int32_t* __restrict__ rp_cat, const int64_t* __restrict__ row_base,
-                                       const int64_t* __restrict__ nnz_base, const int64_t* __restrict__ diag_base,
-                                       int num, int64_t items, int grid, int tpc, int ipt_items, int64_t entries,
-                                       lbk::Split64* out, int64_t* diag) {
+// matrix holding each split's atom: largest m with nnz_base[m] <= j (over all matrices)
+__global__ void split_matrix_kernel(const int2* __restrict__ splits, int64_t entries,
+                                    const int64_t* __restrict__ nnz_base, int num, int32_t* out) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= entries) return;
-  const int64_t d = mp_diag(items, grid, tpc, ipt_items, e);
-  // matrix: largest m in [0, num-1] with diag_base[m] <= d
-  int lo_m = 0, hi_m = num - 1;
-  while (lo_m < hi_m) {
-    const int mid = (lo_m + hi_m + 1) >> 1;
-    if (diag_base[mid] <= d) lo_m = mid;
-    else hi_m = mid - 1;
-  }
-  const int m = lo_m;
-  const int64_t R = row_base[m + 1] - row_base[m];
-  const int64_t N = nnz_base[m + 1] - nnz_base[m];
-  const int64_t dl = d - diag_base[m];
-  const int32_t* rp = rp_cat + row_base[m] + m;
-  int64_t lo = dl - N > 0 ? dl - N : 0;
-  int64_t hi = dl < R ? dl : R;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if ((int64_t)__ldg(rp + mid + 1) > dl - mid - 1) hi = mid;
-    else lo = mid + 1;
-  }
-  lbk::Split64 s;
-  s.i = row_base[m] + lo;
-  s.j = nnz_base[m] + (dl - lo);
-  s.m = m;
-  s.pad = 0;
-  out[e] = s;
-  diag[e] = d;
+  out[e] = lbk::find_matrix(nnz_base, 0, num - 1, (int64_t)splits[e].y);
 }
 
-static lb_status_t alloc_table(MpTable& t, size_t split_bytes) {
-  LB_CUDA_TRY(cudaMalloc(&t.splits, split_bytes * (size_t)t.entries));
+lb_status_t build_mp_table(MpTable& t, const int32_t* rp, int32_t R, int64_t N, int ipt, int variant, int num_sms,
+                           int ctas_per_sm, const BatchBases* batch, cudaStream_t s) {
+  t.release();
+  if (!kernel_tma(ipt, false, false)) {
+    set_error("items_per_thread must be 4, 8 or 16");
+    return LB_ERR_UNSUPPORTED;
+  }
+  if (variant != 0 && variant != 1) {
+    set_error("mp_variant must be 0 or 1");
+    return LB_ERR_UNSUPPORTED;
+  }
+  t.ipt = ipt;
+  t.variant = variant;
+  // 4 items short of the CTA's thread slots: a tile's atoms start up to 3 slots
+  // into its 16-byte aligned window, and all of them must still fall inside
+  // the BLOCK * IPT slots the threads cover
+  t.items_per_tile = kBlock * ipt - 4;
+  t.items = (int64_t)R + N;
+  t.num_tiles = R;
+  const int occ = ctas_per_sm > 0 ? ctas_per_sm : occupancy_mp(ipt, variant);
+  mp_geometry(t.items, num_sms * occ, t.items_per_tile, kBlock, &t.grid, &t.tiles_per_cta);
+  t.entries = (int64_t)t.grid * (t.tiles_per_cta + 1);
+  LB_CUDA_TRY(cudaMalloc(&t.splits, sizeof(int2) * (size_t)t.entries));
   LB_CUDA_TRY(cudaMalloc(&t.d_diag, sizeof(int64_t) * (size_t)t.entries));
   LB_CUDA_TRY(cudaMalloc(&t.carry_val, sizeof(float) * (size_t)t.grid));
-  LB_CUDA_TRY(cudaMalloc(&t.carry_row, sizeof(int64_t) * (size_t)t.grid));
+  LB_CUDA_TRY(cudaMalloc(&t.carry_row, sizeof(int32_t) * (size_t)t.grid));
   LB_CUDA_TRY(cudaMalloc(&t.ticket, sizeof(unsigned)));
-  LB_CUDA_TRY(cudaMemset(t.ticket, 0, sizeof(unsigned)));
-  return LB_OK;
-}
-
-lb_status_t build_mp_table_single(MpTable& t, const int32_t* rp, int32_t R, int64_t N, int ipt, int num_sms,
-                                  int ctas_per_sm, cudaStream_t s) {
-  t.release();
-  t.batch = false;
-  t.ipt = ipt;
-  t.items_per_tile = kBlock * ipt;
-  t.items = (int64_t)R + N;
-  const int occ = ctas_per_sm > 0 ? ctas_per_sm : occupancy_mp(ipt, false);
-  mp_geometry(t.items, num_sms * occ, t.items_per_tile, kBlock, &t.grid, &t.tiles_per_cta);
-  t.entries = (int64_t)t.grid * (t.tiles_per_cta + 1);
-  LB_TRY(alloc_table(t, sizeof(int2)));
+  LB_CUDA_TRY(cudaMemsetAsync(t.ticket, 0, sizeof(unsigned), s));
   const int threads = 256;
-  const int64_t blocks = (t.entries + threads - 1) / threads;
-  mp_splits_single_kernel<<<(unsigned)blocks, threads, 0, s>>>(rp, R, N, t.items, t.grid, t.tiles_per_cta,
-                                                              t.items_per_tile, t.entries,
-                                                              reinterpret_cast<int2*>(t.splits), t.d_diag);
+  const unsigned blocks = (unsigned)((t.entries + threads - 1) / threads);
+  mp_splits_kernel<<<blocks, threads, 0, s>>>(rp, R, N, t.items, t.grid, t.tiles_per_cta, t.items_per_tile,
+                                              t.entries, t.splits, t.d_diag);
   LB_CUDA_TRY(cudaGetLastError());
-  t.built = true;
-  return LB_OK;
-}
-
-lb_status_t build_mp_table_batch(MpTable& t, const BatchSet& b, int ipt, int num_sms, int ctas_per_sm,
-                                 cudaStream_t s) {
-  t.release();
-  t.batch = true;
-  t.ipt = ipt;
-  t.items_per_tile = kBlock * ipt;
-  t.items = b.total_rows + b.total_nnz;
-  const int occ = ctas_per_sm > 0 ? ctas_per_sm : occupancy_mp(ipt, true);
-  mp_geometry(t.items, num_sms * occ, t.items_per_tile, kBlock, &t.grid, &t.tiles_per_cta);
-  t.entries = (int64_t)t.grid * (t.tiles_per_cta + 1);
-  LB_TRY(alloc_table(t, sizeof(lbk::Split64)));
-  const int threads = 256;
-  const int64_t blocks = (t.entries + threads - 1) / threads;
-  mp_splits_batch_kernel<<<(unsigned)blocks, threads, 0, s>>>(
-      b.rp_cat, b.row_base, b.nnz_base, b.diag_base, b.num, t.items, t.grid, t.tiles_per_cta, t.items_per_tile,
-      t.entries, reinterpret_cast<lbk::Split64*>(t.splits), t.d_diag);
-  LB_CUDA_TRY(cudaGetLastError());
+  if (batch) {
+    LB_CUDA_TRY(cudaMalloc(&t.split_m, sizeof(int32_t) * (size_t)t.entries));
+    split_matrix_kernel<<<blocks, threads, 0, s>>>(t.splits, t.entries, batch->nnz_base, batch->num, t.split_m);
+    LB_CUDA_TRY(cudaGetLastError());
+  }
   t.built = true;
   return LB_OK;
 }
 
 // ----------------------------------------------------------------- launches --
 
-static lbk::MpArgs make_args(const MpTable& t, const int32_t* rp, const BatchSet* b, int64_t num_tiles) {
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+static lbk::MpArgs make_args(const MpTable& t, const SpmvCall& c) {
   lbk::MpArgs a{};
-  a.rp = b ? b->rp_cat : rp;
-  a.row_base = b ? b->row_base : nullptr;
-  a.nnz_base = b ? b->nnz_base : nullptr;
-  a.vec_base = b ? b->vec_base : nullptr;
+  a.rp = c.rp;
+  a.atoms = lbk::AtomView{c.idx, c.val, c.perm, c.vec, c.check, c.status};
+  a.out = c.out;
   a.splits = t.splits;
+  a.split_m = c.batch ? t.split_m : nullptr;
+  a.nnz_base = c.batch ? c.batch->nnz_base : nullptr;
+  a.vec_base = c.batch ? c.batch->vec_base : nullptr;
   a.tiles_per_cta = t.tiles_per_cta;
   a.num_ctas = t.grid;
-  a.num_tiles = num_tiles;
+  a.items_per_tile = t.items_per_tile;
+  a.num_tiles = t.num_tiles;
   a.carry_val = t.carry_val;
   a.carry_row = t.carry_row;
   a.ticket = t.ticket;
+  a.status = c.status;
   return a;
 }
 
-static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
-
-template <int IPT, bool BATCH, bool VEC>
-static void mp_launch(const lbk::MpArgs& a, cudaStream_t s) {
-  lbk::mp_spmv_kernel<kBlock, IPT, BATCH, VEC>
-      <<<a.num_ctas, kBlock, lbk::mp_smem_bytes<kBlock, IPT>(), s>>>(a);
-}
-
-template <int IPT, bool BATCH>
-static void mp_launch_v(const lbk::MpArgs& a, bool vec, cudaStream_t s) {
-  static bool attr_set[2] = {false, false};
-  if (!attr_set[vec]) {
-    if (vec) set_mp_smem<IPT, BATCH, true>();
-    else set_mp_smem<IPT, BATCH, false>();
-    attr_set[vec] = true;
-  }
-  if (vec) mp_launch<IPT, BATCH, true>(a, s);
-  else mp_launch<IPT, BATCH, false>(a, s);
-}
-
-lb_status_t launch_mp_spmv(const MpTable& t, const int32_t* rp, const BatchSet* b, const int32_t* idx,
-                           const float* val, const int32_t* perm, const float* vec, float* out, int64_t num_tiles,
-                           int32_t check_cols, int* status, cudaStream_t s) {
+lb_status_t launch_mp_spmv(const MpTable& t, const SpmvCall& c, cudaStream_t s) {
   if (!t.built) {
     set_error("merge-path table not built");
     return LB_ERR_INVALID_ARG;
   }
   if (t.items == 0) return LB_OK;
-  lbk::MpArgs a = make_args(t, rp, b, num_tiles);
-  a.atoms = lbk::AtomView{idx, val, perm, vec, check_cols, status};
-  a.out = out;
-  const bool v = aligned16(idx) && (perm ? aligned16(perm) : aligned16(val));
-  const bool batch = b != nullptr;
-  switch (t.ipt) {
-    case 4:
-      batch ? mp_launch_v<4, true>(a, v, s) : mp_launch_v<4, false>(a, v, s);
-      break;
-    case 8:
-      batch ? mp_launch_v<8, true>(a, v, s) : mp_launch_v<8, false>(a, v, s);
-      break;
-    case 16:
-      batch ? mp_launch_v<16, true>(a, v, s) : mp_launch_v<16, false>(a, v, s);
-      break;
-    default:
-      set_error("items_per_thread must be 4, 8 or 16");
-      return LB_ERR_UNSUPPORTED;
+  if (c.batch && !t.split_m) {
+    set_error("batched launch on a table without matrix indices");
+    return LB_ERR_INVALID_ARG;
   }
-  LB_CUDA_TRY(cudaGetLastError());
+  lbk::MpArgs a = make_args(t, c);
+  const bool xb = c.batch != nullptr;
+  const bool perm = c.perm != nullptr;
+  const bool vec = t.variant == 0 && aligned16(c.idx) && aligned16(c.rp) &&
+                   (perm ? aligned16(c.perm) : aligned16(c.val));
+  cudaError_t e;
+  if (vec) e = launch(kernel_tma(t.ipt, xb, perm), t.grid, tma_smem(t.ipt), s, &a);
+  else e = launch(kernel_plain(t.ipt, xb), t.grid, plain_smem(t.ipt), s, &a);
+  LB_CUDA_TRY(e);
   return LB_OK;
 }
 
-template <int IPT, bool BATCH, bool DV>
-static void ex_launch(const lbk::MpArgs& a, cudaStream_t s) {
-  const size_t smem = sizeof(int) * 2 * kBlock * IPT;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(lbk::mp_expand_kernel<kBlock, IPT, BATCH, DV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    attr = true;
-  }
-  lbk::mp_expand_kernel<kBlock, IPT, BATCH, DV><<<a.num_ctas, kBlock, smem, s>>>(a);
-}
-
-template <int IPT>
-static void ex_dispatch(const lbk::MpArgs& a, bool batch, bool dv, cudaStream_t s) {
-  if (batch) dv ? ex_launch<IPT, true, true>(a, s) : ex_launch<IPT, true, false>(a, s);
-  else dv ? ex_launch<IPT, false, true>(a, s) : ex_launch<IPT, false, false>(a, s);
-}
-
-lb_status_t launch_mp_expand(const MpTable& t, const int32_t* rp, const BatchSet* b, const int32_t* idx,
-                             const float* x, const float* dy, float* dvals, int32_t* tile_of_atom,
-                             int32_t check_cols, int* status, cudaStream_t s) {
+lb_status_t launch_mp_expand(const MpTable& t, const SpmvCall& c, const float* dy, float* dvals,
+                             int32_t* tile_of_atom, cudaStream_t s) {
   if (!t.built) {
     set_error("merge-path table not built");
     return LB_ERR_INVALID_ARG;
   }
   if (t.items == 0) return LB_OK;
-  lbk::MpArgs a = make_args(t, rp, b, 0);
-  a.atoms = lbk::AtomView{idx, nullptr, nullptr, x, check_cols, status};
+  lbk::MpArgs a = make_args(t, c);
   a.dy = dy;
   a.dvals = dvals;
   a.tile_of_atom = tile_of_atom;
-  const bool dv = dvals != nullptr;
-  switch (t.ipt) {
-    case 4: ex_dispatch<4>(a, b != nullptr, dv, s); break;
-    case 8: ex_dispatch<8>(a, b != nullptr, dv, s); break;
-    case 16: ex_dispatch<16>(a, b != nullptr, dv, s); break;
-    default:
-      set_error("items_per_thread must be 4, 8 or 16");
-      return LB_ERR_UNSUPPORTED;
-  }
-  LB_CUDA_TRY(cudaGetLastError());
+  const bool xb = c.batch != nullptr && dvals != nullptr;
+  LB_CUDA_TRY(launch(kernel_expand(t.ipt, xb, dvals != nullptr), t.grid, expand_smem(t.ipt), s, &a));
   return LB_OK;
 }
 
-lb_status_t launch_tm_spmv(const int32_t* rp, int32_t R, const int32_t* idx, const float* val, const int32_t* perm,
-                           const float* vec, float* out, int32_t check_cols, int* status, int num_sms,
-                           cudaStream_t s) {
-  if (R == 0) return LB_OK;
+lb_status_t launch_tm_spmv(const SpmvCall& c, cudaStream_t s) {
+  if (c.num_tiles == 0) return LB_OK;
   // Listing 3 launches ceil(rows / 256) blocks of 256 threads
-  const int64_t blocks = ((int64_t)R + kBlock - 1) / kBlock;
-  (void)num_sms;
-  lbk::tm_spmv_kernel<kBlock><<<(unsigned)blocks, kBlock, 0, s>>>(rp, R, lbk::AtomView{idx, val, perm, vec, check_cols, status}, out);
+  const int64_t blocks = ((int64_t)c.num_tiles + kBlock - 1) / kBlock;
+  lbk::tm_spmv_kernel<kBlock><<<(unsigned)blocks, kBlock, 0, s>>>(
+      c.rp, c.num_tiles, lbk::AtomView{c.idx, c.val, c.perm, c.vec, c.check, c.status}, c.out);
   LB_CUDA_TRY(cudaGetLastError());
   return LB_OK;
 }
 
 template <int G>
-static void gm_launch(int64_t blocks, const int32_t* rp, int32_t R, const lbk::AtomView& at, float* out,
-                      cudaStream_t s) {
-  lbk::gm_spmv_kernel<kBlock, G><<<(unsigned)blocks, kBlock, 0, s>>>(rp, R, at, out);
+static void gm_launch(int64_t blocks, const SpmvCall& c, cudaStream_t s) {
+  lbk::gm_spmv_kernel<kBlock, G><<<(unsigned)blocks, kBlock, 0, s>>>(
+      c.rp, c.num_tiles, lbk::AtomView{c.idx, c.val, c.perm, c.vec, c.check, c.status}, c.out);
 }
 
-lb_status_t launch_gm_spmv(int group, const int32_t* rp, int32_t R, const int32_t* idx, const float* val,
-                           const int32_t* perm, const float* vec, float* out, int32_t check_cols, int* status,
-                           int num_sms, cudaStream_t s) {
-  if (R == 0) return LB_OK;
+lb_status_t launch_gm_spmv(int group, const SpmvCall& c, int num_sms, cudaStream_t s) {
+  if (c.num_tiles == 0) return LB_OK;
   // one chunk of `group` tiles per group, kBlock / group groups per block;
   // oversubscribed grid capped at 64 blocks per SM, grid-stride beyond that
-  int64_t blocks = ((int64_t)R + kBlock - 1) / kBlock;
+  int64_t blocks = ((int64_t)c.num_tiles + kBlock - 1) / kBlock;
   const int64_t cap = (int64_t)num_sms * 64;
   if (blocks > cap) blocks = cap;
-  const lbk::AtomView at{idx, val, perm, vec, check_cols, status};
   switch (group) {
-    case 4: gm_launch<4>(blocks, rp, R, at, out, s); break;
-    case 8: gm_launch<8>(blocks, rp, R, at, out, s); break;
-    case 16: gm_launch<16>(blocks, rp, R, at, out, s); break;
-    case 32: gm_launch<32>(blocks, rp, R, at, out, s); break;
-    case 64: gm_launch<64>(blocks, rp, R, at, out, s); break;
-    case 128: gm_launch<128>(blocks, rp, R, at, out, s); break;
-    case 256: gm_launch<256>(blocks, rp, R, at, out, s); break;
+    case 4: gm_launch<4>(blocks, c, s); break;
+    case 8: gm_launch<8>(blocks, c, s); break;
+    case 16: gm_launch<16>(blocks, c, s); break;
+    case 32: gm_launch<32>(blocks, c, s); break;
+    case 64: gm_launch<64>(blocks, c, s); break;
+    case 128: gm_launch<128>(blocks, c, s); break;
+    case 256: gm_launch<256>(blocks, c, s); break;
     default:
       set_error("group size must be a power of two in [4, 256]");
       return LB_ERR_UNSUPPORTED;

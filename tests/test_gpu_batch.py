@@ -40,14 +40,14 @@ def make_plan(lb, b, **kw):
     return plan, rp_cat, ci, v
 
 
-def check_batch(lb, b, ipts=(8,)):
+def check_batch(lb, b, ipts=(8,), variants=(0, 1)):
     import torch
     xs, dys = batch_inputs(b)
     y64, yb, dx64, dxb, dv32 = oracle_batch(b, xs, dys)
     xd, dyd = to_dev(np.concatenate(xs), np.concatenate(dys))
     row_of = np.concatenate([oracle.row_of_atom(m.rp) for m in b.mats])
-    for ipt in ipts:
-        plan, rp_cat, ci, v = make_plan(lb, b, items_per_thread=ipt)
+    for ipt, var in [(i, v) for i in ipts for v in variants]:
+        plan, rp_cat, ci, v = make_plan(lb, b, items_per_thread=ipt, mp_variant=var)
         ys = [plan.spmv(ci, v, xd) for _ in range(3)]
         assert_within_bound(ys[0].cpu().numpy(), y64, yb, "batch y")
         for y in ys[1:]:

@@ -18,7 +18,10 @@ SCHEDULES = [("thread_mapped", {}), ("warp_mapped", {}), ("block_mapped", {}),
              ("group_mapped", {"group_size": 16}), ("group_mapped", {"group_size": 64}),
              ("group_mapped", {"group_size": 128}),
              ("merge_path", {"items_per_thread": 4}), ("merge_path", {"items_per_thread": 8}),
-             ("merge_path", {"items_per_thread": 16})]
+             ("merge_path", {"items_per_thread": 16}),
+             ("merge_path", {"items_per_thread": 4, "mp_variant": 1}),
+             ("merge_path", {"items_per_thread": 8, "mp_variant": 1}),
+             ("merge_path", {"items_per_thread": 16, "mp_variant": 1})]
 SCHED_IDS = [s + "".join(f"_{k}{v}" for k, v in o.items()) for s, o in SCHEDULES]
 
 
@@ -104,9 +107,9 @@ def test_unaligned_buffers_take_scalar_path(lbmod):
 
 def test_merge_path_splits_bit_exact(lbmod):
     for name, m in small_cases() + edge_cases():
-        for ipt in (4, 8, 16):
+        for ipt, var in ((4, 0), (8, 0), (16, 0), (8, 1)):
             rp = to_dev(m.rp)[0]
-            plan = lbmod.Plan(rp, m.nnz, "merge_path", items_per_thread=ipt)
+            plan = lbmod.Plan(rp, m.nnz, "merge_path", items_per_thread=ipt, mp_variant=var)
             diag, ij = plan.splits()
             info = plan.info()
             R, N = m.num_rows, m.nnz
