@@ -435,13 +435,30 @@ def run_ours(args, ws, rank, local):
     step_ms = max_over_ranks(step_ms_local, ws, device)
     value = ws * byts / (step_ms * 1e-3) / 1e9
 
+    # ceiling of this column pattern: stream the same atoms and gather x, nothing else
+    n_probe = N - (N % 4)
+    pgrid = lib.lb_probe_gather_grid()
+    probe_out = torch.empty(max(1, pgrid) * 256, device=device)
+
+    def probe(i):
+        _lib.check(lib.lb_probe_gather(vp(ci_d[i % copies].data_ptr()), vp(v_d[i % copies].data_ptr()),
+                                       vp(x_d.data_ptr()), n_probe, vp(probe_out.data_ptr()), pgrid, vp(sp)),
+                   "lb_probe_gather")
+    for i in range(3):
+        probe(i)
+    probe_ms = statistics.median(time_launches(torch, probe, 20 if args.ncu else 50, stream))
+
     peak, peak_kind = measured_peaks()
     kern_ms = statistics.median(durs)
     achieved = byts / (kern_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": profiled_traffic(),
-                "peak_kind": f"{peak_kind} HBM copy", "kernel": "mp_spmv_tma_kernel",
-                "kernel_ms_median": round(kern_ms, 5), "frac_of_8TBps_spec": round(achieved / 8000.0, 4)}
+                "peak_kind": f"{peak_kind} HBM copy", "kernel": "mp_spmv_warp_kernel",
+                "kernel_ms_median": round(kern_ms, 5), "frac_of_8TBps_spec": round(achieved / 8000.0, 4),
+                "gather_ceiling": {"probe": "lb_probe_gather: stream the same col_idx/vals, gather x, nothing else",
+                                   "probe_ms": round(probe_ms, 5),
+                                   "spmv_GBps_at_ceiling": round(byts / (probe_ms * 1e-3) / 1e9, 2),
+                                   "frac": round(probe_ms / kern_ms, 4)}}
 
     print(f"[bench] merge-path {value:.1f} GB/s ({step_ms * 1e3:.2f} us/step), kernel {achieved:.1f} GB/s, "
           f"parity {parity_ok}", file=sys.stderr, flush=True)
@@ -451,7 +468,9 @@ def run_ours(args, ws, rank, local):
         for s, kw in (("thread_mapped", {}), ("warp_mapped", {}), ("block_mapped", {}),
                       ("group_mapped", {"group_size": 8}), ("merge_path", {"items_per_thread": 4}),
                       ("merge_path", {"items_per_thread": 16}),
-                      ("merge_path", {"items_per_thread": 8, "mp_variant": 1})):
+                      ("merge_path", {"items_per_thread": 8, "mp_variant": 1}),
+                      ("merge_path", {"items_per_thread": 8, "mp_variant": 2}),
+                      ("merge_path", {"items_per_thread": 4, "mp_variant": 2})):
             ps = plans_for(s, **kw)
             ln = launcher(ps)
             for i in range(3):

@@ -78,10 +78,12 @@ typedef struct lb_plan_opts_t {
   int32_t validate;         /* nonzero: lb_plan checks tile_offsets on the device (tile_offsets[0] = 0,
                                nondecreasing, last = num_atoms -> LB_ERR_INVALID_ARG); kernels check every
                                column index against num_cols and record LB_ERR_BAD_INPUT for lb_status */
-  int32_t mp_variant;       /* merge-path work split inside a CTA tile: 0 = rows and atoms dealt to the
-                               threads in two passes, streamed by bulk copies (needs 16-byte aligned
-                               buffers, else 1 is used); 1 = each thread searches its own diagonal and
-                               walks its IPT items in merge order (Sec. 5.2.1 per thread) */
+  int32_t mp_variant;       /* merge-path worker: 0 = warps (each warp walks its equal share in tiles of
+                               32*IPT-4 items; its lanes take the tile's rows and atoms evenly in two
+                               passes); 1 = CTAs whose threads each search their own diagonal and walk
+                               IPT items in merge order (the per-thread form of Sec. 5.2.1); 2 = CTAs
+                               with a bulk-copy (TMA) ring and the two-pass split (needs 16-byte aligned
+                               buffers, else 1 is used) */
   int32_t reserved[2];
 } lb_plan_opts_t;
 
@@ -92,8 +94,11 @@ typedef struct lb_plan_info_t {
   int64_t num_atoms;
   int32_t block_threads;    /* threads per CTA */
   int32_t grid;             /* CTAs launched per SpMV */
-  int32_t items_per_tile;   /* merge-path: rows + atoms per CTA tile (block_threads * items_per_thread - 4) */
-  int32_t tiles_per_cta;    /* merge-path: tiles walked by each persistent CTA */
+  int32_t items_per_tile;   /* merge-path: rows + atoms per tile (32 * items_per_thread - 4 for warp
+                               workers, block_threads * items_per_thread - 4 for CTA workers) */
+  int32_t tiles_per_cta;    /* merge-path: tiles walked by each worker */
+  int32_t num_workers;      /* merge-path: owners of the equal shares (warps or CTAs) */
+  int32_t mp_variant;       /* merge-path: the worker variant in use */
   int64_t num_splits;       /* merge-path: entries in the split table */
   int32_t group_size;       /* group-mapped schedules */
   int32_t num_sms;
@@ -229,7 +234,7 @@ lb_schedule_t lb_heuristic_schedule(int32_t rows, int32_t cols, int64_t nnz);
 
 /*
  * The diagonals a merge-path plan splits at, as a pure host function:
- * `grid` persistent CTAs take equal shares [floor(c*items/grid),
+ * `grid` persistent workers take equal shares [floor(c*items/grid),
  * floor((c+1)*items/grid)) of the items = rows + atoms, each share cut into
  * tiles of items_per_tile; entry c*(tiles_per_cta+1)+k is
  * min(share_begin(c) + k*items_per_tile, share_end(c)), with
@@ -238,6 +243,19 @@ lb_schedule_t lb_heuristic_schedule(int32_t rows, int32_t cols, int64_t nnz);
  */
 lb_status_t lb_merge_diagonals(int64_t items, int32_t grid, int32_t items_per_tile, int64_t* host_diag, size_t cap,
                                size_t* count, int32_t* tiles_per_cta);
+
+/*
+ * Measurement probe for the roofline of this path (no counterpart in the
+ * paper): streams idx[n] and vals[n] (16-byte aligned, n a multiple of 4) and
+ * gathers x[idx[k]], reducing sum vals[k] * x[idx[k]] to one float per thread
+ * into out[grid * 256] (grid = 0 picks 4 CTAs per SM).  Its time is the
+ * fastest the hardware streams the atoms and gathers the dense vector in that
+ * order, the ceiling for SpMV with the same column pattern.  Async, no
+ * allocation.  LB_ERR_INVALID_ARG for unaligned pointers or n % 4 != 0.
+ */
+lb_status_t lb_probe_gather(const int32_t* idx, const float* vals, const float* x, int64_t n, float* out,
+                            int32_t grid, void* stream);
+int32_t lb_probe_gather_grid(void);
 
 const char* lb_status_string(lb_status_t status);
 const char* lb_last_error(void);

@@ -33,7 +33,8 @@ class PlanOpts(ctypes.Structure):
 class PlanInfo(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int32), ("num_tiles", ctypes.c_int32), ("num_cols", ctypes.c_int32),
                 ("num_atoms", ctypes.c_int64), ("block_threads", ctypes.c_int32), ("grid", ctypes.c_int32),
-                ("items_per_tile", ctypes.c_int32), ("tiles_per_cta", ctypes.c_int32), ("num_splits", ctypes.c_int64),
+                ("items_per_tile", ctypes.c_int32), ("tiles_per_cta", ctypes.c_int32), ("num_workers", ctypes.c_int32),
+                ("mp_variant", ctypes.c_int32), ("num_splits", ctypes.c_int64),
                 ("group_size", ctypes.c_int32), ("num_sms", ctypes.c_int32), ("kernels_per_spmv", ctypes.c_int32),
                 ("has_transpose", ctypes.c_int32)]
 
@@ -59,6 +60,8 @@ SIGNATURES = {
     "lb_batch_spmv_backward": (I32, [VP, VP, VP, VP, VP, VP, VP, VP]),
     "lb_heuristic_schedule": (I32, [I32, I32, I64]),
     "lb_merge_diagonals": (I32, [I64, I32, I32, VP, SZ, ctypes.POINTER(SZ), ctypes.POINTER(I32)]),
+    "lb_probe_gather": (I32, [VP, VP, VP, I64, VP, I32, VP]),
+    "lb_probe_gather_grid": (I32, []),
     "lb_status_string": (ctypes.c_char_p, [I32]),
     "lb_last_error": (ctypes.c_char_p, []),
     "lb_version": (I32, []),

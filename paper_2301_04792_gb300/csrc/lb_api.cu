@@ -24,6 +24,29 @@ __global__ void check_columns_kernel(const int32_t* __restrict__ ci, int64_t n, 
   }
 }
 
+// Roofline probe: stream idx / vals as 16-byte vectors and gather x, nothing else.
+__global__ void __launch_bounds__(256) probe_gather_kernel(const int4* __restrict__ idx, const float4* __restrict__ v,
+                                                           const float* __restrict__ x, int64_t n4,
+                                                           float* __restrict__ out) {
+  float acc = 0.f;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += 2 * stride) {
+    const int64_t k = i + stride;
+    const int4 c0 = __ldcs(idx + i);
+    const float4 w0 = __ldcs(v + i);
+    int4 c1 = make_int4(0, 0, 0, 0);
+    float4 w1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (k < n4) {
+      c1 = __ldcs(idx + k);
+      w1 = __ldcs(v + k);
+    }
+    acc += w0.x * __ldg(x + c0.x) + w0.y * __ldg(x + c0.y) + w0.z * __ldg(x + c0.z) + w0.w * __ldg(x + c0.w);
+    if (k < n4)
+      acc += w1.x * __ldg(x + c1.x) + w1.y * __ldg(x + c1.y) + w1.z * __ldg(x + c1.z) + w1.w * __ldg(x + c1.w);
+  }
+  out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
 unsigned blocks_for(int64_t n, int threads, int64_t cap = 65536LL * 16) {
   int64_t b = (n + threads - 1) / threads;
   if (b > cap) b = cap;
@@ -83,6 +106,30 @@ extern "C" {
 const char* lb_last_error(void) { return g_last_error.c_str(); }
 
 int32_t lb_version(void) { return 10000; }
+
+int32_t lb_probe_gather_grid(void) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  return 4 * device_sms(dev);
+}
+
+lb_status_t lb_probe_gather(const int32_t* idx, const float* vals, const float* x, int64_t n, float* out,
+                            int32_t grid, void* stream) {
+  if (!idx || !vals || !x || !out || n < 0 || (n & 3) || (reinterpret_cast<uintptr_t>(idx) & 15) ||
+      (reinterpret_cast<uintptr_t>(vals) & 15)) {
+    set_error("lb_probe_gather: need 16-byte aligned idx and vals and n % 4 == 0");
+    return LB_ERR_INVALID_ARG;
+  }
+  if (grid <= 0) grid = lb_probe_gather_grid();
+  if (grid <= 0) {
+    set_error("lb_probe_gather: no device");
+    return LB_ERR_CUDA;
+  }
+  probe_gather_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      reinterpret_cast<const int4*>(idx), reinterpret_cast<const float4*>(vals), x, n / 4, out);
+  LB_CUDA_TRY(cudaGetLastError());
+  return LB_OK;
+}
 
 const char* lb_status_string(lb_status_t s) {
   switch (s) {
@@ -235,6 +282,8 @@ lb_status_t lb_plan_get_info(lb_plan_t p, lb_plan_info_t* info) {
   info->block_threads = kBlock;
   info->items_per_tile = p->mp.items_per_tile;
   info->tiles_per_cta = p->mp.tiles_per_cta;
+  info->num_workers = p->mp.workers;
+  info->mp_variant = p->mp.variant;
   info->num_splits = p->mp.entries;
   info->group_size = p->group_size;
   info->num_sms = p->num_sms;

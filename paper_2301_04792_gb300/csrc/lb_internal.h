@@ -37,10 +37,11 @@ constexpr int kBlock = 256;
 struct MpTable {
   bool built = false;
   int ipt = 8;
-  int variant = 0;  // lb_plan_opts_t.mp_variant
+  int variant = 0;  // lb_plan_opts_t.mp_variant: 0 warp workers, 1 per-thread search, 2 CTA tiles + bulk copies
   int items_per_tile = 0;
-  int grid = 0;
-  int tiles_per_cta = 0;
+  int grid = 0;          // CTAs launched
+  int workers = 0;       // owners of split-table shares (warps for variant 0, CTAs otherwise)
+  int tiles_per_cta = 0; // tiles per worker
   int64_t entries = 0;
   int64_t items = 0;
   int32_t num_tiles = 0;

@@ -180,12 +180,14 @@ struct MpArgs {
   const int32_t* split_m;   // batch: matrix of every split's atom (nullptr otherwise)
   const int64_t* nnz_base;  // batch: first atom of each matrix
   const int64_t* vec_base;  // batch: first dense-vector entry of each matrix
-  int tiles_per_cta;
-  int num_ctas;
+  int tiles_per_cta;         // tiles per worker (a worker is a CTA or, for the warp kernels, a warp)
+  int num_ctas;              // CTAs launched
+  int num_workers;           // split-table owners = carry slots
   int items_per_tile;
   int32_t num_tiles;
-  float* carry_val;         // [num_ctas]
-  int32_t* carry_row;       // [num_ctas]
+  int64_t num_atoms;         // length of the atom arrays (bounds of vector loads)
+  float* carry_val;         // [num_workers]
+  int32_t* carry_row;       // [num_workers]
   unsigned* ticket;         // zero between launches
   int* status;
   // expand kernels
@@ -231,19 +233,20 @@ __device__ __forceinline__ int tile_search(End end, int d, int nrows, int nnz) {
   return lo;
 }
 
-// Fix-up of rows split between CTAs, run by the last CTA to finish: y[row] +=
-// the carries of all CTAs that left `row` open, combined in CTA order by a
-// segmented scan keyed by row.  Resets the ticket for the next launch.
+// Fix-up of rows split between workers, run by the last CTA to finish:
+// y[row] += the carries of all workers that left `row` open, combined in
+// worker order by a segmented scan keyed by row.  Resets the ticket for the
+// next launch.
 template <int BLOCK>
 __device__ __forceinline__ void last_cta_fixup(const MpArgs& a, float* s_wv, int* s_wf, float* s_incl) {
   float run = 0.f;
-  for (int b = 0; b < a.num_ctas; b += BLOCK) {
+  for (int b = 0; b < a.num_workers; b += BLOCK) {
     const int e = b + threadIdx.x;
-    const bool valid = e < a.num_ctas;
+    const bool valid = e < a.num_workers;
     const int row = valid ? __ldcg(a.carry_row + e) : -2;
     const float val = valid ? __ldcg(a.carry_val + e) : 0.f;
     const int prev = (e == 0) ? -3 : (valid ? __ldcg(a.carry_row + e - 1) : -2);
-    const int next = (e + 1 < a.num_ctas) ? __ldcg(a.carry_row + e + 1) : -4;
+    const int next = (e + 1 < a.num_workers) ? __ldcg(a.carry_row + e + 1) : -4;
     float excl, total;
     const float incl = block_seg_scan<BLOCK>(val, row != prev, run, s_wv, s_wf, s_incl, excl, total);
     if (valid && row >= 0 && row != next) {
@@ -256,8 +259,19 @@ __device__ __forceinline__ void last_cta_fixup(const MpArgs& a, float* s_wv, int
   if (threadIdx.x == 0) *a.ticket = 0u;
 }
 
-// Carry-out of a CTA and the ticket that elects the last CTA.  Returns true in
-// the last CTA (all threads).
+// Ticket that elects the last CTA to finish, after every thread of this CTA
+// has written its carries.  Returns true in the last CTA (all threads).
+__device__ __forceinline__ bool cta_ticket(const MpArgs& a, int* s_last) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) *s_last = (atomicAdd(a.ticket, 1u) == (unsigned)(a.num_ctas - 1));
+  __syncthreads();
+  const bool last = *s_last != 0;
+  if (last) __threadfence();
+  return last;
+}
+
+// Carry-out of a CTA worker (the CTA-tile kernels) and the ticket.
 template <int BLOCK>
 __device__ __forceinline__ bool publish_carry(const MpArgs& a, int32_t open_row, float carry, int* s_last) {
   if (threadIdx.x == 0) {
@@ -696,6 +710,326 @@ __global__ void __launch_bounds__(BLOCK) mp_expand_kernel(MpArgs a) {
     }
     __syncthreads();
     cur = nxt;
+  }
+}
+
+// -------------------------------------------------- warp-worker merge path --
+
+// Per-warp shared scratch of the warp-worker kernels: one bit per slot of the
+// warp tile marking the slot that holds a row's last atom, the row of each
+// marked slot, and the tile's row results.
+template <int IPT>
+struct WarpScratch {
+  static constexpr int W = 32 * IPT;
+  unsigned bits[IPT];  // W / 32 words
+  int endrow[W];
+  float y[W];
+};
+
+// Atom indices and values (or perm) of this lane's IPT slots of a warp tile:
+// slot s holds atom a_lo + s, a_lo = first atom rounded down to a multiple of
+// 4, so each lane's slots are whole 16-byte vectors.  Vectors wholly inside
+// the array are loaded as int4; a ragged end of the array with scalars.
+// Vectors wholly past the tile's last atom are skipped.
+template <int IPT>
+__device__ __forceinline__ void load_lane_atoms(const int32_t* __restrict__ idx, const int32_t* __restrict__ val,
+                                                int64_t a_lo, int s0, int64_t j_end, int64_t n, int* c, int* vb) {
+#pragma unroll
+  for (int u = 0; u < IPT / 4; ++u) {
+    const int64_t g4 = a_lo + s0 + 4 * u;
+    if (g4 >= j_end) {
+      c[4 * u] = c[4 * u + 1] = c[4 * u + 2] = c[4 * u + 3] = 0;
+      vb[4 * u] = vb[4 * u + 1] = vb[4 * u + 2] = vb[4 * u + 3] = 0;
+    } else if (g4 + 3 < n) {
+      const int4 ci4 = ld_stream(reinterpret_cast<const int4*>(idx + g4));
+      const int4 vb4 = ld_stream(reinterpret_cast<const int4*>(val + g4));
+      c[4 * u] = ci4.x;
+      c[4 * u + 1] = ci4.y;
+      c[4 * u + 2] = ci4.z;
+      c[4 * u + 3] = ci4.w;
+      vb[4 * u] = vb4.x;
+      vb[4 * u + 1] = vb4.y;
+      vb[4 * u + 2] = vb4.z;
+      vb[4 * u + 3] = vb4.w;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int64_t g = g4 + e;
+        c[4 * u + e] = g < n ? ld_stream(idx + g) : 0;
+        vb[4 * u + e] = g < n ? ld_stream(val + g) : 0;
+      }
+    }
+  }
+}
+
+// Row pass of a warp tile: rows [i0, i0 + nrows) whose ends fall in the tile.
+// An empty row gets 0, a first row that closes at the tile's first atom gets
+// the running carry; every other row marks the slot of its last atom.  Lane l
+// takes rows l, l + 32, ...; the previous row's end comes from the next-lower
+// lane (a shuffle) instead of a second load.
+template <int IPT, bool WRITE_Y>
+__device__ __forceinline__ void warp_row_pass(const int32_t* __restrict__ rp, int i0, int nrows, int j0, int off,
+                                              float carry, WarpScratch<IPT>& sc) {
+  const int lane = threadIdx.x & 31;
+  int last_e = -1;  // end of row r - 32 seen by lane 31, carried to lane 0
+  for (int rb = 0; rb < nrows; rb += 32) {
+    const int r = rb + lane;
+    const int e = r < nrows ? __ldg(rp + i0 + 1 + r) - j0 : 0;
+    int pe = __shfl_up_sync(kFull, e, 1);
+    if (lane == 0) pe = last_e;
+    last_e = __shfl_sync(kFull, e, 31);
+    if (r < nrows) {
+      if (r > 0 && e == pe) {
+        if (WRITE_Y) sc.y[r] = 0.f;
+      } else if (e == 0) {
+        if (WRITE_Y) sc.y[r] = carry;
+      } else {
+        const int slot = e - 1 + off;
+        sc.endrow[slot] = r;
+        atomicOr(&sc.bits[slot >> 5], 1u << (slot & 31));
+      }
+    }
+  }
+}
+
+// The split-table entries of one warp, held 32 at a time in lane registers
+// (lane l holds entry 32 * chunk + l) and handed out by shuffles.
+struct WarpSplits {
+  const int2* sp;
+  int count;  // entries owned by the warp
+  int chunk = -1;
+  int2 reg;
+  __device__ __forceinline__ int2 get(int e) {
+    const int lane = threadIdx.x & 31;
+    const int ch = e >> 5;
+    if (ch != chunk) {
+      chunk = ch;
+      const int idx = ch * 32 + lane;
+      reg = idx < count ? __ldg(sp + idx) : make_int2(0, 0);
+    }
+    return make_int2(__shfl_sync(kFull, reg.x, e & 31), __shfl_sync(kFull, reg.y, e & 31));
+  }
+};
+
+// Merge-path SpMV (Sec. 5.2.1) with warps as the workers.  The plan's split
+// table gives every warp an equal share of rows + atoms, cut into warp tiles
+// of 32 * IPT - 4 merge items, each split found by the search along its
+// diagonal.  A warp walks its share tile by tile with no block-wide barrier:
+// per tile its lanes gather the dense vector for the tile's atoms (loaded as
+// 16-byte vectors one tile ahead), split the tile's rows evenly (row pass:
+// empty rows 0, marks at each row's last atom) and its atoms evenly (IPT
+// consecutive atoms per lane, closing a row at each mark); a warp-shuffle
+// segmented scan in lane order, with the warp's running carry in front,
+// resolves rows that cross lanes.  Rows split between warps are fixed up by
+// the last CTA to finish.
+// VEC: idx and val (or perm) are 16-byte aligned (vector loads); otherwise
+// every atom is loaded on its own.
+template <int IPT, bool XB, bool PERM, bool VEC>
+__global__ void __launch_bounds__(256) mp_spmv_warp_kernel(MpArgs a) {
+  static_assert(IPT % 4 == 0 && 32 % IPT == 0, "IPT must be 4, 8 or 16");
+  constexpr int WPB = 8;
+  __shared__ WarpScratch<IPT> sc_all[WPB];
+  __shared__ float s_wv[WPB];
+  __shared__ int s_wf[WPB];
+  __shared__ float s_incl[256];
+  __shared__ int s_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int w = blockIdx.x * WPB + warp;
+  WarpScratch<IPT>& sc = sc_all[warp];
+  const AtomView& at = a.atoms;
+  const int32_t* vsrc = PERM ? at.perm : reinterpret_cast<const int32_t*>(at.val);
+
+  WarpSplits spl{a.splits + (size_t)w * (a.tiles_per_cta + 1), a.tiles_per_cta + 1};
+  const int32_t* sm = XB ? a.split_m + (size_t)w * (a.tiles_per_cta + 1) : nullptr;
+  int2 c0 = spl.get(0);
+  int ntiles;
+  {
+    const int2 e1 = __ldg(a.splits + (size_t)w * (a.tiles_per_cta + 1) + a.tiles_per_cta);
+    const int64_t share = (int64_t)(e1.x - c0.x) + (e1.y - c0.y);
+    ntiles = (int)((share + a.items_per_tile - 1) / a.items_per_tile);
+  }
+  if (lane < IPT) sc.bits[lane] = 0u;
+  __syncwarp();
+
+  const int s0 = lane * IPT;
+  // this lane's atom indices and values (or perm) of a tile
+  auto load_atoms = [&](int2 t0, int2 t1, int* c, int* vb) {
+    const int j0 = t0.y, off = j0 & 3, nnz = t1.y - t0.y;
+    if constexpr (VEC) {
+      load_lane_atoms<IPT>(at.idx, vsrc, (int64_t)(j0 - off), s0, t1.y, a.num_atoms, c, vb);
+    } else {
+#pragma unroll
+      for (int q = 0; q < IPT; ++q) {
+        const int l = s0 + q - off;
+        const bool in = (unsigned)l < (unsigned)nnz;
+        c[q] = in ? ld_stream(at.idx + j0 + l) : 0;
+        vb[q] = in ? ld_stream(vsrc + j0 + l) : 0;
+      }
+    }
+  };
+
+  float carry = 0.f;
+  int c_cur[IPT], vb_cur[IPT];
+  int2 c1 = c0;
+  if (ntiles > 0) {
+    c1 = spl.get(1);
+    load_atoms(c0, c1, c_cur, vb_cur);
+  }
+  for (int k = 0; k < ntiles; ++k) {
+    const int nrows = c1.x - c0.x, nnz = c1.y - c0.y, j0 = c0.y, off = j0 & 3;
+    // gathers of tile k
+    int m0 = 0, m1 = 0;
+    int64_t xb0 = 0;
+    if constexpr (XB) {
+      m0 = __ldg(sm + k);
+      m1 = __ldg(sm + k + 1);
+      xb0 = __ldg(a.vec_base + m0);
+    }
+    float xg[IPT], vv[IPT];
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) {
+      const int l = s0 + q - off;
+      xg[q] = 0.f;
+      vv[q] = 0.f;
+      if ((unsigned)l < (unsigned)nnz) {
+        xg[q] = at.gather(c_cur[q], atom_xbase<XB>(a, m0, m1, xb0, (int64_t)j0 + l));
+        vv[q] = PERM ? __ldg(at.val + vb_cur[q]) : __int_as_float(vb_cur[q]);
+      }
+    }
+    // atoms of tile k + 1, in flight while tile k is reduced
+    int2 c2 = c1;
+    if (k + 1 < ntiles) {
+      c2 = spl.get(k + 2);
+      load_atoms(c1, c2, c_cur, vb_cur);
+    }
+    warp_row_pass<IPT, true>(a.rp, c0.x, nrows, j0, off, carry, sc);
+    const float prefix = (nrows > 0 && __ldg(a.rp + c0.x + 1) == j0) ? 0.f : carry;
+    __syncwarp();
+
+    const unsigned bits = sc.bits[s0 >> 5] >> (s0 & 31);
+    float acc = 0.f, first = 0.f;
+    int any = 0, first_row = 0;
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) {
+      acc += vv[q] * xg[q];
+      if ((bits >> q) & 1u) {
+        const int r = sc.endrow[s0 + q];
+        if (any) {
+          sc.y[r] = acc;
+        } else {
+          first = acc;
+          first_row = r;
+          any = 1;
+        }
+        acc = 0.f;
+      }
+    }
+    // segmented scan over the lanes, the warp's carry in front of lane 0
+    float v = acc;
+    int f = any;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const float vo = __shfl_up_sync(kFull, v, o);
+      const int fo = __shfl_up_sync(kFull, f, o);
+      if (lane >= o) {
+        if (!f) v = vo + v;
+        f |= fo;
+      }
+    }
+    if (!f) v = prefix + v;
+    const float up = __shfl_up_sync(kFull, v, 1);
+    const float excl = lane ? up : prefix;
+    carry = __shfl_sync(kFull, v, 31);
+    if (any) sc.y[first_row] = excl + first;
+    __syncwarp();
+    for (int r = lane; r < nrows; r += 32) a.out[c0.x + r] = sc.y[r];
+    if (lane < IPT) sc.bits[lane] = 0u;
+    __syncwarp();
+    c0 = c1;
+    c1 = c2;
+  }
+  if (lane == 0) {
+    a.carry_row[w] = c0.x < a.num_tiles ? c0.x : -1;
+    a.carry_val[w] = carry;
+  }
+  if (!cta_ticket(a, &s_last)) return;
+  last_cta_fixup<256>(a, s_wv, s_wf, s_incl);
+}
+
+// Warp-worker expand: the tile of every atom from the same row marks, then
+// per atom either tile_of_atom[j] = tile or dvals[j] = dy[tile] * x[col[j]]
+// (one correctly rounded FP32 product).  The tile of an atom is the row of
+// the first marked slot at or after it (the row left open at the tile's end
+// if there is none).
+template <int IPT, bool XB, bool DVALS>
+__global__ void __launch_bounds__(256) mp_expand_warp_kernel(MpArgs a) {
+  constexpr int WPB = 8;
+  __shared__ WarpScratch<IPT> sc_all[WPB];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int w = blockIdx.x * WPB + warp;
+  WarpScratch<IPT>& sc = sc_all[warp];
+  const int2* sp = a.splits + (size_t)w * (a.tiles_per_cta + 1);
+  const int32_t* sm = XB ? a.split_m + (size_t)w * (a.tiles_per_cta + 1) : nullptr;
+  int2 c0 = __ldg(sp);
+  const int2 e1 = __ldg(sp + a.tiles_per_cta);
+  const int64_t share = (int64_t)(e1.x - c0.x) + (e1.y - c0.y);
+  const int ntiles = (int)((share + a.items_per_tile - 1) / a.items_per_tile);
+  if (lane < IPT) sc.bits[lane] = 0u;
+  __syncwarp();
+  const int s0 = lane * IPT;
+  for (int k = 0; k < ntiles; ++k) {
+    const int2 c1 = __ldg(sp + k + 1);
+    const int nrows = c1.x - c0.x, nnz = c1.y - c0.y, j0 = c0.y, off = j0 & 3;
+    int c[IPT];
+    if constexpr (DVALS) {
+#pragma unroll
+      for (int q = 0; q < IPT; ++q) {
+        const int l = s0 + q - off;
+        c[q] = (unsigned)l < (unsigned)nnz ? ld_stream(a.atoms.idx + j0 + l) : 0;
+      }
+    }
+    warp_row_pass<IPT, false>(a.rp, c0.x, nrows, j0, off, 0.f, sc);
+    __syncwarp();
+    const unsigned bits = (sc.bits[s0 >> 5] >> (s0 & 31)) & (IPT == 32 ? 0xffffffffu : ((1u << IPT) - 1u));
+    // first marked slot of each later lane: suffix minimum over the lanes
+    int fm = bits ? s0 + __ffs(bits) - 1 : INT_MAX;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int n = __shfl_down_sync(kFull, fm, o);
+      if (lane + o < 32) fm = min(fm, n);
+    }
+    int nxt = __shfl_down_sync(kFull, fm, 1);
+    if (lane == 31) nxt = INT_MAX;
+    int rows_q[IPT];
+#pragma unroll
+    for (int q = IPT - 1; q >= 0; --q) {
+      if ((bits >> q) & 1u) nxt = s0 + q;
+      rows_q[q] = nxt == INT_MAX ? c1.x : c0.x + sc.endrow[nxt];
+    }
+    int m0 = 0, m1 = 0;
+    int64_t xb0 = 0;
+    if constexpr (XB && DVALS) {
+      m0 = __ldg(sm + k);
+      m1 = __ldg(sm + k + 1);
+      xb0 = __ldg(a.vec_base + m0);
+    }
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) {
+      const int l = s0 + q - off;
+      if ((unsigned)l < (unsigned)nnz) {
+        const int64_t j = (int64_t)j0 + l;
+        if constexpr (DVALS) {
+          const float xv = a.atoms.gather(c[q], atom_xbase<XB>(a, m0, m1, xb0, j));
+          __stcs(a.dvals + j, __fmul_rn(__ldg(a.dy + rows_q[q]), xv));
+        } else {
+          a.tile_of_atom[j] = rows_q[q];
+        }
+      }
+    }
+    __syncwarp();
+    if (lane < IPT) sc.bits[lane] = 0u;
+    __syncwarp();
+    c0 = c1;
   }
 }
 

@@ -76,6 +76,45 @@ static void* expand_fn() {
   return reinterpret_cast<void*>(lbk::mp_expand_kernel<kBlock, IPT, XB, DV>);
 }
 
+template <int IPT, bool XB, bool PERM, bool VEC>
+static void* warp_fn() {
+  return reinterpret_cast<void*>(lbk::mp_spmv_warp_kernel<IPT, XB, PERM, VEC>);
+}
+template <int IPT, bool XB, bool DV>
+static void* expand_warp_fn() {
+  return reinterpret_cast<void*>(lbk::mp_expand_warp_kernel<IPT, XB, DV>);
+}
+template <int IPT>
+static void* pick_warp(bool xb, bool perm, bool vec) {
+  if (vec) {
+    if (xb) return perm ? warp_fn<IPT, true, true, true>() : warp_fn<IPT, true, false, true>();
+    return perm ? warp_fn<IPT, false, true, true>() : warp_fn<IPT, false, false, true>();
+  }
+  if (xb) return perm ? warp_fn<IPT, true, true, false>() : warp_fn<IPT, true, false, false>();
+  return perm ? warp_fn<IPT, false, true, false>() : warp_fn<IPT, false, false, false>();
+}
+template <int IPT>
+static void* pick_expand_warp(bool xb, bool dv) {
+  if (xb) return dv ? expand_warp_fn<IPT, true, true>() : expand_warp_fn<IPT, true, false>();
+  return dv ? expand_warp_fn<IPT, false, true>() : expand_warp_fn<IPT, false, false>();
+}
+static void* kernel_warp(int ipt, bool xb, bool perm, bool vec) {
+  switch (ipt) {
+    case 4: return pick_warp<4>(xb, perm, vec);
+    case 8: return pick_warp<8>(xb, perm, vec);
+    case 16: return pick_warp<16>(xb, perm, vec);
+  }
+  return nullptr;
+}
+static void* kernel_expand_warp(int ipt, bool xb, bool dv) {
+  switch (ipt) {
+    case 4: return pick_expand_warp<4>(xb, dv);
+    case 8: return pick_expand_warp<8>(xb, dv);
+    case 16: return pick_expand_warp<16>(xb, dv);
+  }
+  return nullptr;
+}
+
 template <int IPT>
 static void* pick_tma(bool xb, bool perm) {
   if (xb) return perm ? tma_fn<IPT, true, true>() : tma_fn<IPT, true, false>();
@@ -136,9 +175,10 @@ static cudaError_t launch(void* fn, int grid, size_t smem, cudaStream_t s, lbk::
 }
 
 int occupancy_mp(int ipt, int variant) {
-  void* fn = variant == 1 ? kernel_plain(ipt, false) : kernel_tma(ipt, false, false);
+  void* fn = variant == 0 ? kernel_warp(ipt, false, false, true)
+             : variant == 1 ? kernel_plain(ipt, false) : kernel_tma(ipt, false, false);
   if (!fn) return 1;
-  const size_t smem = variant == 1 ? plain_smem(ipt) : tma_smem(ipt);
+  const size_t smem = variant == 0 ? 0 : variant == 1 ? plain_smem(ipt) : tma_smem(ipt);
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kBlock, smem) != cudaSuccess || occ < 1) occ = 1;
@@ -179,30 +219,45 @@ lb_status_t build_mp_table(MpTable& t, const int32_t* rp, int32_t R, int64_t N, 
     set_error("items_per_thread must be 4, 8 or 16");
     return LB_ERR_UNSUPPORTED;
   }
-  if (variant != 0 && variant != 1) {
-    set_error("mp_variant must be 0 or 1");
+  if (variant < 0 || variant > 2) {
+    set_error("mp_variant must be 0, 1 or 2");
     return LB_ERR_UNSUPPORTED;
   }
   t.ipt = ipt;
   t.variant = variant;
-  // 4 items short of the CTA's thread slots: a tile's atoms start up to 3 slots
-  // into its 16-byte aligned window, and all of them must still fall inside
-  // the BLOCK * IPT slots the threads cover
-  t.items_per_tile = kBlock * ipt - 4;
   t.items = (int64_t)R + N;
   t.num_tiles = R;
   const int occ = ctas_per_sm > 0 ? ctas_per_sm : occupancy_mp(ipt, variant);
-  mp_geometry(t.items, num_sms * occ, t.items_per_tile, kBlock, &t.grid, &t.tiles_per_cta);
-  t.entries = (int64_t)t.grid * (t.tiles_per_cta + 1);
+  if (variant == 0) {
+    // warps are the workers: 8 per CTA, at least 32 items (one per lane) each on average
+    constexpr int kWarps = kBlock / 32;
+    t.items_per_tile = 32 * ipt - 4;
+    int64_t ctas = (t.items + kBlock - 1) / kBlock;
+    if (ctas > (int64_t)num_sms * occ) ctas = (int64_t)num_sms * occ;
+    if (ctas < 1) ctas = 1;
+    t.grid = (int)ctas;
+    t.workers = t.grid * kWarps;
+    const int64_t share = (t.items + t.workers - 1) / t.workers;
+    int64_t tpc = (share + t.items_per_tile - 1) / t.items_per_tile;
+    t.tiles_per_cta = (int)(tpc < 1 ? 1 : tpc);
+  } else {
+    // 4 items short of the CTA's thread slots: a tile's atoms start up to 3
+    // slots into their 16-byte aligned window, and all of them must still fall
+    // inside the BLOCK * IPT slots the threads cover
+    t.items_per_tile = kBlock * ipt - 4;
+    mp_geometry(t.items, num_sms * occ, t.items_per_tile, kBlock, &t.grid, &t.tiles_per_cta);
+    t.workers = t.grid;
+  }
+  t.entries = (int64_t)t.workers * (t.tiles_per_cta + 1);
   LB_CUDA_TRY(cudaMalloc(&t.splits, sizeof(int2) * (size_t)t.entries));
   LB_CUDA_TRY(cudaMalloc(&t.d_diag, sizeof(int64_t) * (size_t)t.entries));
-  LB_CUDA_TRY(cudaMalloc(&t.carry_val, sizeof(float) * (size_t)t.grid));
-  LB_CUDA_TRY(cudaMalloc(&t.carry_row, sizeof(int32_t) * (size_t)t.grid));
+  LB_CUDA_TRY(cudaMalloc(&t.carry_val, sizeof(float) * (size_t)t.workers));
+  LB_CUDA_TRY(cudaMalloc(&t.carry_row, sizeof(int32_t) * (size_t)t.workers));
   LB_CUDA_TRY(cudaMalloc(&t.ticket, sizeof(unsigned)));
   LB_CUDA_TRY(cudaMemsetAsync(t.ticket, 0, sizeof(unsigned), s));
   const int threads = 256;
   const unsigned blocks = (unsigned)((t.entries + threads - 1) / threads);
-  mp_splits_kernel<<<blocks, threads, 0, s>>>(rp, R, N, t.items, t.grid, t.tiles_per_cta, t.items_per_tile,
+  mp_splits_kernel<<<blocks, threads, 0, s>>>(rp, R, N, t.items, t.workers, t.tiles_per_cta, t.items_per_tile,
                                               t.entries, t.splits, t.d_diag);
   LB_CUDA_TRY(cudaGetLastError());
   if (batch) {
@@ -229,8 +284,10 @@ static lbk::MpArgs make_args(const MpTable& t, const SpmvCall& c) {
   a.vec_base = c.batch ? c.batch->vec_base : nullptr;
   a.tiles_per_cta = t.tiles_per_cta;
   a.num_ctas = t.grid;
+  a.num_workers = t.workers;
   a.items_per_tile = t.items_per_tile;
   a.num_tiles = t.num_tiles;
+  a.num_atoms = t.items - t.num_tiles;
   a.carry_val = t.carry_val;
   a.carry_row = t.carry_row;
   a.ticket = t.ticket;
@@ -251,11 +308,15 @@ lb_status_t launch_mp_spmv(const MpTable& t, const SpmvCall& c, cudaStream_t s) 
   lbk::MpArgs a = make_args(t, c);
   const bool xb = c.batch != nullptr;
   const bool perm = c.perm != nullptr;
-  const bool vec = t.variant == 0 && aligned16(c.idx) && aligned16(c.rp) &&
-                   (perm ? aligned16(c.perm) : aligned16(c.val));
+  const bool vec_atoms = aligned16(c.idx) && (perm ? aligned16(c.perm) : aligned16(c.val));
   cudaError_t e;
-  if (vec) e = launch(kernel_tma(t.ipt, xb, perm), t.grid, tma_smem(t.ipt), s, &a);
-  else e = launch(kernel_plain(t.ipt, xb), t.grid, plain_smem(t.ipt), s, &a);
+  if (t.variant == 0) {
+    e = launch(kernel_warp(t.ipt, xb, perm, vec_atoms), t.grid, 0, s, &a);
+  } else if (t.variant == 2 && vec_atoms && aligned16(c.rp)) {
+    e = launch(kernel_tma(t.ipt, xb, perm), t.grid, tma_smem(t.ipt), s, &a);
+  } else {
+    e = launch(kernel_plain(t.ipt, xb), t.grid, plain_smem(t.ipt), s, &a);
+  }
   LB_CUDA_TRY(e);
   return LB_OK;
 }
@@ -272,7 +333,10 @@ lb_status_t launch_mp_expand(const MpTable& t, const SpmvCall& c, const float* d
   a.dvals = dvals;
   a.tile_of_atom = tile_of_atom;
   const bool xb = c.batch != nullptr && dvals != nullptr;
-  LB_CUDA_TRY(launch(kernel_expand(t.ipt, xb, dvals != nullptr), t.grid, expand_smem(t.ipt), s, &a));
+  if (t.variant == 0)
+    LB_CUDA_TRY(launch(kernel_expand_warp(t.ipt, xb, dvals != nullptr), t.grid, 0, s, &a));
+  else
+    LB_CUDA_TRY(launch(kernel_expand(t.ipt, xb, dvals != nullptr), t.grid, expand_smem(t.ipt), s, &a));
   return LB_OK;
 }
 

@@ -21,7 +21,10 @@ SCHEDULES = [("thread_mapped", {}), ("warp_mapped", {}), ("block_mapped", {}),
              ("merge_path", {"items_per_thread": 16}),
              ("merge_path", {"items_per_thread": 4, "mp_variant": 1}),
              ("merge_path", {"items_per_thread": 8, "mp_variant": 1}),
-             ("merge_path", {"items_per_thread": 16, "mp_variant": 1})]
+             ("merge_path", {"items_per_thread": 16, "mp_variant": 1}),
+             ("merge_path", {"items_per_thread": 4, "mp_variant": 2}),
+             ("merge_path", {"items_per_thread": 8, "mp_variant": 2}),
+             ("merge_path", {"items_per_thread": 16, "mp_variant": 2})]
 SCHED_IDS = [s + "".join(f"_{k}{v}" for k, v in o.items()) for s, o in SCHEDULES]
 
 
@@ -107,14 +110,14 @@ def test_unaligned_buffers_take_scalar_path(lbmod):
 
 def test_merge_path_splits_bit_exact(lbmod):
     for name, m in small_cases() + edge_cases():
-        for ipt, var in ((4, 0), (8, 0), (16, 0), (8, 1)):
+        for ipt, var in ((4, 0), (8, 0), (16, 0), (8, 1), (4, 2), (16, 2)):
             rp = to_dev(m.rp)[0]
             plan = lbmod.Plan(rp, m.nnz, "merge_path", items_per_thread=ipt, mp_variant=var)
             diag, ij = plan.splits()
             info = plan.info()
             R, N = m.num_rows, m.nnz
             # the plan's diagonals follow the documented layout
-            d_host, tpc = lbmod.merge_diagonals(R + N, info["grid"], info["items_per_tile"])
+            d_host, tpc = lbmod.merge_diagonals(R + N, info["num_workers"], info["items_per_tile"])
             assert tpc == info["tiles_per_cta"]
             assert np.array_equal(diag, d_host), name
             assert np.array_equal(ij, oracle.merge_splits(diag, m.rp)), f"{name} ipt={ipt}"
@@ -123,9 +126,10 @@ def test_merge_path_splits_bit_exact(lbmod):
 def test_atom_tiles_bit_exact(lbmod):
     for name, m in small_cases() + edge_cases():
         rp = to_dev(m.rp)[0]
-        plan = lbmod.Plan(rp, m.nnz, "thread_mapped")
-        got = plan.atom_tiles().cpu().numpy()
-        assert np.array_equal(got, oracle.row_of_atom(m.rp)), name
+        for var in (0, 1, 2):
+            plan = lbmod.Plan(rp, m.nnz, "thread_mapped", mp_variant=var)
+            got = plan.atom_tiles().cpu().numpy()
+            assert np.array_equal(got, oracle.row_of_atom(m.rp)), (name, var)
 
 
 def test_validation_reports_bad_inputs(lbmod):
