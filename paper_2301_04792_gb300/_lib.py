@@ -53,6 +53,7 @@ SIGNATURES = {
     "lb_plan_transpose": (I32, [VP, VP, VP, VP, VP]),
     "lb_spmv_backward": (I32, [VP, I32, VP, VP, VP, VP, VP, VP, VP]),
     "lb_atom_tiles": (I32, [VP, VP, VP]),
+    "lb_spmv_noalloc": (I32, [VP, I32, I32, VP, VP, VP, VP, VP]),
     "lb_status": (I32, [VP, VP]),
     "lb_batch_plan": (I32, [PLANP, I32, VP, VP, VP, VP, ctypes.POINTER(PlanOpts), VP]),
     "lb_batch_spmv": (I32, [VP, VP, VP, VP, VP, VP]),
