@@ -6,7 +6,7 @@
 
 #include <string>
 
-#include "../../include/lb.h"
+#include "lb.h"
 
 namespace lbh {
 

@@ -233,27 +233,58 @@ __device__ __forceinline__ int tile_search(End end, int d, int nrows, int nnz) {
   return lo;
 }
 
-// Fix-up of rows split between workers, run by the last CTA to finish:
-// y[row] += the carries of all workers that left `row` open, combined in
-// worker order by a segmented scan keyed by row.  Resets the ticket for the
-// next launch.
+// Fix-up of rows split between CTAs, run by the last CTA to finish:
+// y[row] += the carries of all CTAs that left `row` open, combined in
+// CTA order.  The carries are taken in passes of BLOCK * 8: each thread
+// loads 8 consecutive carries at once and sums the runs of equal rows in its
+// slice, a block segmented scan (thread order, the previous pass's open run in
+// front) joins runs that cross threads, and the thread holding a run's last
+// carry updates its row.  Resets the ticket for the next launch.
 template <int BLOCK>
 __device__ __forceinline__ void last_cta_fixup(const MpArgs& a, float* s_wv, int* s_wf, float* s_incl) {
-  float run = 0.f;
-  for (int b = 0; b < a.num_workers; b += BLOCK) {
-    const int e = b + threadIdx.x;
-    const bool valid = e < a.num_workers;
-    const int row = valid ? __ldcg(a.carry_row + e) : -2;
-    const float val = valid ? __ldcg(a.carry_val + e) : 0.f;
-    const int prev = (e == 0) ? -3 : (valid ? __ldcg(a.carry_row + e - 1) : -2);
-    const int next = (e + 1 < a.num_workers) ? __ldcg(a.carry_row + e + 1) : -4;
-    float excl, total;
-    const float incl = block_seg_scan<BLOCK>(val, row != prev, run, s_wv, s_wf, s_incl, excl, total);
-    if (valid && row >= 0 && row != next) {
-      float* py = a.out + row;
-      __stcg(py, __ldcg(py) + incl);
+  constexpr int KC = 8;
+  const int P = a.num_ctas;  // one carry slot per CTA
+  float run_in = 0.f;  // open run at the end of the previous pass
+  for (int base = 0; base < P; base += BLOCK * KC) {
+    const int e0 = base + threadIdx.x * KC;
+    int row[KC];
+    float val[KC];
+#pragma unroll
+    for (int q = 0; q < KC; ++q) {
+      const int e = e0 + q;
+      row[q] = e < P ? __ldcg(a.carry_row + e) : -2;
+      val[q] = e < P ? __ldcg(a.carry_val + e) : 0.f;
     }
-    run = total;
+    const int prev = e0 == 0 ? -3 : (e0 - 1 < P ? __ldcg(a.carry_row + e0 - 1) : -2);
+    const int next = e0 + KC < P ? __ldcg(a.carry_row + e0 + KC) : -4;
+    // this slice: does a run start in it, and the sum of its last (open) run
+    float tail = 0.f;
+    int head = 0, pr = prev;
+#pragma unroll
+    for (int q = 0; q < KC; ++q) {
+      if (row[q] != pr) {
+        head = 1;
+        tail = val[q];
+      } else {
+        tail = tail + val[q];
+      }
+      pr = row[q];
+    }
+    float excl, total;
+    block_seg_scan<BLOCK>(tail, head, run_in, s_wv, s_wf, s_incl, excl, total);
+    float run = excl;
+    pr = prev;
+#pragma unroll
+    for (int q = 0; q < KC; ++q) {
+      run = (row[q] != pr) ? val[q] : run + val[q];
+      pr = row[q];
+      const int nx = q + 1 < KC ? row[q + 1] : next;
+      if (row[q] >= 0 && row[q] != nx) {
+        float* py = a.out + row[q];
+        __stcg(py, __ldcg(py) + run);
+      }
+    }
+    run_in = total;
     __syncthreads();
   }
   if (threadIdx.x == 0) *a.ticket = 0u;
@@ -331,7 +362,6 @@ template <int BLOCK, int IPT, bool XB, bool PERM>
 __global__ void __launch_bounds__(BLOCK) mp_spmv_tma_kernel(MpArgs a) {
   static_assert(IPT % 4 == 0 && 32 % IPT == 0, "IPT must be 4, 8 or 16");
   using L = MpLayout<BLOCK, IPT>;
-  constexpr int T = L::T;
   constexpr int W = L::W;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   int* s_ring = reinterpret_cast<int*>(smem_raw);
@@ -576,7 +606,7 @@ __global__ void __launch_bounds__(BLOCK) mp_spmv_tma_kernel(MpArgs a) {
 template <int BLOCK, int IPT, bool XB>
 __global__ void __launch_bounds__(BLOCK) mp_spmv_plain_kernel(MpArgs a) {
   constexpr int T = BLOCK * IPT;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   float* s_prod = reinterpret_cast<float*>(smem_raw);  // T
   int* s_end = reinterpret_cast<int*>(s_prod + T);     // T
   float* s_y = reinterpret_cast<float*>(s_end + T);    // T
@@ -658,7 +688,7 @@ constexpr size_t mp_plain_smem_bytes() {
 template <int BLOCK, int IPT, bool XB, bool DVALS>
 __global__ void __launch_bounds__(BLOCK) mp_expand_kernel(MpArgs a) {
   constexpr int T = BLOCK * IPT;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   int* s_end = reinterpret_cast<int*>(smem_raw);  // T
   int* s_row = s_end + T;                          // T
   const int tid = threadIdx.x;
@@ -833,6 +863,8 @@ __global__ void __launch_bounds__(256) mp_spmv_warp_kernel(MpArgs a) {
   __shared__ int s_wf[WPB];
   __shared__ float s_incl[256];
   __shared__ int s_last;
+  __shared__ int s_crow[WPB];
+  __shared__ float s_cval[WPB];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int w = blockIdx.x * WPB + warp;
   WarpScratch<IPT>& sc = sc_all[warp];
@@ -948,9 +980,33 @@ __global__ void __launch_bounds__(256) mp_spmv_warp_kernel(MpArgs a) {
     c0 = c1;
     c1 = c2;
   }
+  // Carries between the CTA's own warps (consecutive workers) are settled here,
+  // by every CTA at its end: a segmented scan over the 8 warps' carries keyed
+  // by row; a run that a later warp of this CTA closed is added to its row,
+  // the run left open by the last warp becomes the CTA's carry-out.
   if (lane == 0) {
-    a.carry_row[w] = c0.x < a.num_tiles ? c0.x : -1;
-    a.carry_val[w] = carry;
+    s_crow[warp] = c0.x < a.num_tiles ? c0.x : -1;
+    s_cval[warp] = carry;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const int row = lane < WPB ? s_crow[lane] : -5;
+    float v = lane < WPB ? s_cval[lane] : 0.f;
+#pragma unroll
+    for (int o = 1; o < WPB; o <<= 1) {
+      const float vo = __shfl_up_sync(kFull, v, o, WPB);
+      const int ro = __shfl_up_sync(kFull, row, o, WPB);
+      if ((lane & (WPB - 1)) >= o && ro == row) v = vo + v;
+    }
+    const int nrow = __shfl_down_sync(kFull, row, 1, WPB);
+    if (lane < WPB - 1 && row >= 0 && nrow != row) {
+      float* py = a.out + row;
+      __stcg(py, __ldcg(py) + v);
+    }
+    if (lane == WPB - 1) {
+      a.carry_row[blockIdx.x] = row;
+      a.carry_val[blockIdx.x] = v;
+    }
   }
   if (!cta_ticket(a, &s_last)) return;
   last_cta_fixup<256>(a, s_wv, s_wf, s_incl);
