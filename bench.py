@@ -266,6 +266,8 @@ def bench_batched(torch, lb, W, device, reps=5):
     vp = ctypes.c_void_p
     f4, i4 = 4, 4
 
+    calls_list = []
+
     def plain_calls(stream_ptr):
         calls = []
         for p, rs, cs, ns, cm in plans:
@@ -277,6 +279,7 @@ def bench_batched(torch, lb, W, device, reps=5):
             dxv = vp(dx.data_ptr() + f4 * int(cs.start))
             dvv = vp(dv.data_ptr() + f4 * int(ns.start))
             calls.append((p.handle, civ, vv, xv, yv, dyv, dxv, dvv, cm))
+        calls_list[:] = calls
         sp_ = vp(stream_ptr)
 
         def run():
@@ -328,6 +331,20 @@ def bench_batched(torch, lb, W, device, reps=5):
     t_plain = timed(plain_step)
     t_plain_graph = timed(gp.replay)
     t_batch = timed(g.replay)
+    # the three passes on their own (batched launch vs. the 64 per-matrix launches)
+    parts = {}
+    for name, bfn, pfn in (
+            ("fwd", lambda: bp.spmv(ci, v, x, y),
+             lambda: [_lib.check(lib.lb_spmv(c[0], c[1], c[2], c[3], c[4], vp(0)), "lb_spmv") for c in calls_list]),
+            ("dx", lambda: bp.backward(ci, v, x, dy, want_dvals=False, dx_cat=dx),
+             lambda: [_lib.check(lib.lb_spmv_backward(c[0], c[8], c[1], c[2], c[3], c[5], c[6], None, vp(0)), "bwd")
+                      for c in calls_list]),
+            ("dvals", lambda: bp.backward(ci, v, x, dy, want_dx=False, dvals_cat=dv),
+             lambda: [_lib.check(lib.lb_spmv_backward(c[0], c[8], c[1], c[2], c[3], c[5], None, c[7], vp(0)), "bwd")
+                      for c in calls_list])):
+        bfn()
+        pfn()
+        parts[name] = {"batched_ms": round(timed(bfn), 4), "plain_ms": round(timed(pfn), 4)}
     fwd = spmv_bytes(R, C, N) - 4 * (b.num - 1)  # rp_cat has one offset array per matrix
     bwd_dx = 12 * N + 4 * (C + b.num) + 4 * R + 4 * C
     bwd_dv = 8 * N + 4 * (R + b.num) + 4 * R + 4 * C
@@ -336,7 +353,7 @@ def bench_batched(torch, lb, W, device, reps=5):
            "plain_ms": round(t_plain, 4), "batched_graph_ms": round(t_batch, 4),
            "speedup": round(t_plain / t_batch, 4), "plain_graph_ms": round(t_plain_graph, 4),
            "speedup_vs_plain_graph": round(t_plain_graph / t_batch, 4),
-           "plain_launches": 3 * b.num, "batched_launches": 3,
+           "plain_launches": 3 * b.num, "batched_launches": 3, "parts": parts,
            "fwd_bwd_bytes": byts, "batched_GBps": round(byts / (t_batch * 1e-3) / 1e9, 2),
            "plain_GBps": round(byts / (t_plain * 1e-3) / 1e9, 2)}
     for p, *_ in plans:

@@ -84,7 +84,10 @@ typedef struct lb_plan_opts_t {
                                IPT items in merge order (the per-thread form of Sec. 5.2.1); 2 = CTAs
                                with a bulk-copy (TMA) ring and the two-pass split (needs 16-byte aligned
                                buffers, else 1 is used) */
-  int32_t reserved[2];
+  int32_t wave_items;       /* batches, warp workers: minimum rows + atoms of a wave (a run of whole
+                               matrices shared out over all workers before the next run starts; keeps
+                               the run's vectors in L2); 0 = max(4 Mi, 2 x workers x items_per_tile) */
+  int32_t reserved[1];
 } lb_plan_opts_t;
 
 /* What a plan resolved to (for tests, the autotuner and reporting). */
@@ -99,6 +102,8 @@ typedef struct lb_plan_info_t {
   int32_t tiles_per_cta;    /* merge-path: tiles walked by each worker */
   int32_t num_workers;      /* merge-path: owners of the equal shares (warps or CTAs) */
   int32_t mp_variant;       /* merge-path: the worker variant in use */
+  int32_t num_waves;        /* merge-path: waves of the forward table (1 unless a batch is cut in waves) */
+  int32_t num_waves_t;      /* merge-path: waves of the transposed table (0 before lb_*prepare_backward) */
   int64_t num_splits;       /* merge-path: entries in the split table */
   int32_t group_size;       /* group-mapped schedules */
   int32_t num_sms;

@@ -27,14 +27,15 @@ STATUS_NAMES = {0: "LB_OK", 1: "LB_ERR_INVALID_ARG", 2: "LB_ERR_CUDA", 3: "LB_ER
 class PlanOpts(ctypes.Structure):
     _fields_ = [("num_cols", ctypes.c_int32), ("items_per_thread", ctypes.c_int32), ("group_size", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("validate", ctypes.c_int32), ("mp_variant", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("wave_items", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class PlanInfo(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int32), ("num_tiles", ctypes.c_int32), ("num_cols", ctypes.c_int32),
                 ("num_atoms", ctypes.c_int64), ("block_threads", ctypes.c_int32), ("grid", ctypes.c_int32),
                 ("items_per_tile", ctypes.c_int32), ("tiles_per_cta", ctypes.c_int32), ("num_workers", ctypes.c_int32),
-                ("mp_variant", ctypes.c_int32), ("num_splits", ctypes.c_int64),
+                ("mp_variant", ctypes.c_int32), ("num_waves", ctypes.c_int32), ("num_waves_t", ctypes.c_int32),
+                ("num_splits", ctypes.c_int64),
                 ("group_size", ctypes.c_int32), ("num_sms", ctypes.c_int32), ("kernels_per_spmv", ctypes.c_int32),
                 ("has_transpose", ctypes.c_int32)]
 

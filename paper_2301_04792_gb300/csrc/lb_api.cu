@@ -284,6 +284,8 @@ lb_status_t lb_plan_get_info(lb_plan_t p, lb_plan_info_t* info) {
   info->tiles_per_cta = p->mp.tiles_per_cta;
   info->num_workers = p->mp.workers;
   info->mp_variant = p->mp.variant;
+  info->num_waves = p->mp.num_waves;
+  info->num_waves_t = p->has_t ? p->mp_t.num_waves : 0;
   info->num_splits = p->mp.entries;
   info->group_size = p->group_size;
   info->num_sms = p->num_sms;

@@ -155,8 +155,10 @@ lb_status_t lb_batch_plan(lb_plan_t* out, int32_t num_mats, const int32_t* host_
   if (st != LB_OK) return fail(st, "");
   if (h) return fail(LB_ERR_INVALID_ARG, "lb_batch_plan: a matrix's offsets leave [0, nnz]");
   p->rp = p->rp_global;
+  std::vector<int64_t> items(num_mats + 1);
+  for (int m = 0; m <= num_mats; ++m) items[m] = rows[m] + nnz[m];
   st = build_mp_table(p->mp, p->rp_global, p->num_tiles, p->num_atoms, o.items_per_thread, o.mp_variant, p->num_sms,
-                      o.ctas_per_sm, &p->bb, s);
+                      o.ctas_per_sm, &p->bb, s, items.data(), rows.data(), num_mats, o.wave_items);
   if (st != LB_OK) return fail(st, "");
   if (cudaStreamSynchronize(s) != cudaSuccess) return fail(LB_ERR_CUDA, "lb_batch_plan: split kernel failed");
   cudaFree(d_rows);
@@ -225,8 +227,15 @@ lb_status_t lb_batch_prepare_backward(lb_plan_t p, const int32_t* col_cat, void*
   cleanup();
   keys = row_of = nullptr;
   bad = nullptr;
+  // the transposed batch: matrix m has cols[m] tiles and the same atoms
+  const int num = p->bb.num;
+  std::vector<int64_t> hc(num + 1), hn(num + 1), titems(num + 1);
+  if (cudaMemcpy(hc.data(), p->bb.vec_base, sizeof(int64_t) * (num + 1), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(hn.data(), p->bb.nnz_base, sizeof(int64_t) * (num + 1), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(LB_ERR_CUDA, "lb_batch_prepare_backward: copy of matrix bases failed");
+  for (int m = 0; m <= num; ++m) titems[m] = hc[m] + hn[m];
   st = build_mp_table(p->mp_t, p->cp, C, N, p->opts.items_per_thread, p->opts.mp_variant, p->num_sms,
-                      p->opts.ctas_per_sm, nullptr, s);
+                      p->opts.ctas_per_sm, nullptr, s, titems.data(), hc.data(), num, p->opts.wave_items);
   if (st != LB_OK) return fail(st, "");
   if (cudaStreamSynchronize(s) != cudaSuccess) return fail(LB_ERR_CUDA, "lb_batch_prepare_backward: sync failed");
   p->has_t = true;

@@ -48,9 +48,11 @@ struct MpTable {
   int2* splits = nullptr;
   int64_t* d_diag = nullptr;  // diagonal of every entry (kept for lb_plan_splits)
   int32_t* split_m = nullptr;
-  float* carry_val = nullptr;
+  int num_waves = 1;          // batched tables: runs of whole matrices processed in order
+  void* d_waves = nullptr;    // lbk::WaveDesc[num_waves] when num_waves > 1
+  float* carry_val = nullptr; // [num_waves x grid]
   int32_t* carry_row = nullptr;
-  unsigned* ticket = nullptr;
+  unsigned* ticket = nullptr; // [num_waves]
   void release();
 };
 
@@ -108,8 +110,13 @@ struct lb_plan_s {
 namespace lbh {
 
 // merge-path tables and launches (lb_merge.cu)
+// item_prefix (optional, batches): prefix of each matrix's rows + atoms on the
+// merge path; with warp workers the table is then cut into waves of whole
+// matrices processed one after another.
 lb_status_t build_mp_table(MpTable& t, const int32_t* rp, int32_t R, int64_t N, int ipt, int variant, int num_sms,
-                           int ctas_per_sm, const BatchBases* batch, cudaStream_t s);
+                           int ctas_per_sm, const BatchBases* batch, cudaStream_t s,
+                           const int64_t* item_prefix = nullptr, const int64_t* row_prefix = nullptr,
+                           int num_mats = 0, int wave_items = 0);
 lb_status_t launch_mp_spmv(const MpTable& t, const SpmvCall& c, cudaStream_t s);
 // dvals[j] = dy[row(j)] * x[idx[j]] (dvals != null) or tile_of_atom[j] = row(j)
 lb_status_t launch_mp_expand(const MpTable& t, const SpmvCall& c, const float* dy, float* dvals,

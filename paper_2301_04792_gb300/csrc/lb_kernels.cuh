@@ -169,6 +169,15 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t
 
 // ------------------------------------------------------------ merge path --
 
+// One wave of a batched merge-path table: a run of whole matrices whose items
+// are shared out evenly over all workers; its split entries start at
+// entry_base, `tpc` tiles per worker.
+struct WaveDesc {
+  int64_t entry_base;
+  int32_t tpc;
+  int32_t row_end;  // first row after the wave: no carry may name it (its rows belong to the next wave)
+};
+
 // Arguments of the merge-path kernels.  `splits` holds, for every persistent
 // CTA c, tiles_per_cta + 1 consecutive (row, atom) splits: the boundaries of
 // its tiles, each on the diagonal given by the plan.
@@ -186,8 +195,10 @@ struct MpArgs {
   int items_per_tile;
   int32_t num_tiles;
   int64_t num_atoms;         // length of the atom arrays (bounds of vector loads)
-  float* carry_val;         // [num_workers]
-  int32_t* carry_row;       // [num_workers]
+  const WaveDesc* waves;    // batched tables: the waves in order; nullptr = one wave
+  int num_waves;
+  float* carry_val;         // [num_waves x num_ctas]
+  int32_t* carry_row;       // [num_waves x num_ctas]
   unsigned* ticket;         // zero between launches
   int* status;
   // expand kernels
@@ -241,9 +252,12 @@ __device__ __forceinline__ int tile_search(End end, int d, int nrows, int nnz) {
 // front) joins runs that cross threads, and the thread holding a run's last
 // carry updates its row.  Resets the ticket for the next launch.
 template <int BLOCK>
-__device__ __forceinline__ void last_cta_fixup(const MpArgs& a, float* s_wv, int* s_wf, float* s_incl) {
+__device__ __forceinline__ void last_cta_fixup(const MpArgs& a, int num_slots, float* s_wv, int* s_wf,
+                                               float* s_incl) {
   constexpr int KC = 8;
-  const int P = a.num_ctas;  // one carry slot per CTA
+  const int P = num_slots;  // one carry slot per CTA and wave, waves in order: rows never decrease
+  const int32_t* carry_row = a.carry_row;
+  const float* carry_val = a.carry_val;
   float run_in = 0.f;  // open run at the end of the previous pass
   for (int base = 0; base < P; base += BLOCK * KC) {
     const int e0 = base + threadIdx.x * KC;
@@ -252,11 +266,11 @@ __device__ __forceinline__ void last_cta_fixup(const MpArgs& a, float* s_wv, int
 #pragma unroll
     for (int q = 0; q < KC; ++q) {
       const int e = e0 + q;
-      row[q] = e < P ? __ldcg(a.carry_row + e) : -2;
-      val[q] = e < P ? __ldcg(a.carry_val + e) : 0.f;
+      row[q] = e < P ? __ldcg(carry_row + e) : -2;
+      val[q] = e < P ? __ldcg(carry_val + e) : 0.f;
     }
-    const int prev = e0 == 0 ? -3 : (e0 - 1 < P ? __ldcg(a.carry_row + e0 - 1) : -2);
-    const int next = e0 + KC < P ? __ldcg(a.carry_row + e0 + KC) : -4;
+    const int prev = e0 == 0 ? -3 : (e0 - 1 < P ? __ldcg(carry_row + e0 - 1) : -2);
+    const int next = e0 + KC < P ? __ldcg(carry_row + e0 + KC) : -4;
     // this slice: does a run start in it, and the sum of its last (open) run
     float tail = 0.f;
     int head = 0, pr = prev;
@@ -597,7 +611,7 @@ __global__ void __launch_bounds__(BLOCK) mp_spmv_tma_kernel(MpArgs a) {
       mbar_wait_bounded(&s_bar[t % kStages], (uint32_t)((t / kStages) & 1));
   }
   if (!publish_carry<BLOCK>(a, open_row, carry, &s_last)) return;
-  last_cta_fixup<BLOCK>(a, s_wv, s_wf, s_incl);
+  last_cta_fixup<BLOCK>(a, a.num_ctas, s_wv, s_wf, s_incl);
 }
 
 // Merge-path SpMV without bulk copies, for buffers that are not 16-byte
@@ -673,7 +687,7 @@ __global__ void __launch_bounds__(BLOCK) mp_spmv_plain_kernel(MpArgs a) {
     cur = nxt;
   }
   if (!publish_carry<BLOCK>(a, cur.x, carry, &s_last)) return;
-  last_cta_fixup<BLOCK>(a, s_wv, s_wf, s_incl);
+  last_cta_fixup<BLOCK>(a, a.num_ctas, s_wv, s_wf, s_incl);
 }
 
 template <int BLOCK, int IPT>
@@ -855,7 +869,7 @@ struct WarpSplits {
 // VEC: idx and val (or perm) are 16-byte aligned (vector loads); otherwise
 // every atom is loaded on its own.
 template <int IPT, bool XB, bool PERM, bool VEC>
-__global__ void __launch_bounds__(256) mp_spmv_warp_kernel(MpArgs a) {
+__global__ void __launch_bounds__(256, IPT <= 8 ? 4 : 2) mp_spmv_warp_kernel(MpArgs a) {
   static_assert(IPT % 4 == 0 && 32 % IPT == 0, "IPT must be 4, 8 or 16");
   constexpr int WPB = 8;
   __shared__ WarpScratch<IPT> sc_all[WPB];
@@ -863,27 +877,38 @@ __global__ void __launch_bounds__(256) mp_spmv_warp_kernel(MpArgs a) {
   __shared__ int s_wf[WPB];
   __shared__ float s_incl[256];
   __shared__ int s_last;
-  __shared__ int s_crow[WPB];
-  __shared__ float s_cval[WPB];
+  __shared__ int s_crow[2][WPB];  // by wave parity: a warp may write its next wave's carry while
+  __shared__ float s_cval[2][WPB];  // warp 0 still reads this wave's
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int w = blockIdx.x * WPB + warp;
   WarpScratch<IPT>& sc = sc_all[warp];
   const AtomView& at = a.atoms;
   const int32_t* vsrc = PERM ? at.perm : reinterpret_cast<const int32_t*>(at.val);
 
-  WarpSplits spl{a.splits + (size_t)w * (a.tiles_per_cta + 1), a.tiles_per_cta + 1};
-  const int32_t* sm = XB ? a.split_m + (size_t)w * (a.tiles_per_cta + 1) : nullptr;
+  if (lane < IPT) sc.bits[lane] = 0u;
+  __syncwarp();
+  const int s0 = lane * IPT;
+  const int nwaves = a.waves ? a.num_waves : 1;
+  for (int wave = 0; wave < nwaves; ++wave) {
+  int64_t ebase = 0;
+  int tpc = a.tiles_per_cta;
+  int row_end = a.num_tiles;
+  if (a.waves) {
+    ebase = a.waves[wave].entry_base;
+    tpc = a.waves[wave].tpc;
+    row_end = a.waves[wave].row_end;
+  }
+  const size_t wbase = (size_t)ebase + (size_t)w * (tpc + 1);
+  WarpSplits spl{a.splits + wbase, tpc + 1};
+  const int32_t* sm = XB ? a.split_m + wbase : nullptr;
   int2 c0 = spl.get(0);
   int ntiles;
   {
-    const int2 e1 = __ldg(a.splits + (size_t)w * (a.tiles_per_cta + 1) + a.tiles_per_cta);
+    const int2 e1 = __ldg(a.splits + wbase + tpc);
     const int64_t share = (int64_t)(e1.x - c0.x) + (e1.y - c0.y);
     ntiles = (int)((share + a.items_per_tile - 1) / a.items_per_tile);
   }
-  if (lane < IPT) sc.bits[lane] = 0u;
-  __syncwarp();
 
-  const int s0 = lane * IPT;
   // this lane's atom indices and values (or perm) of a tile
   auto load_atoms = [&](int2 t0, int2 t1, int* c, int* vb) {
     const int j0 = t0.y, off = j0 & 3, nnz = t1.y - t0.y;
@@ -985,13 +1010,13 @@ __global__ void __launch_bounds__(256) mp_spmv_warp_kernel(MpArgs a) {
   // by row; a run that a later warp of this CTA closed is added to its row,
   // the run left open by the last warp becomes the CTA's carry-out.
   if (lane == 0) {
-    s_crow[warp] = c0.x < a.num_tiles ? c0.x : -1;
-    s_cval[warp] = carry;
+    s_crow[wave & 1][warp] = c0.x < row_end ? c0.x : -1;
+    s_cval[wave & 1][warp] = carry;
   }
   __syncthreads();
   if (warp == 0) {
-    const int row = lane < WPB ? s_crow[lane] : -5;
-    float v = lane < WPB ? s_cval[lane] : 0.f;
+    const int row = lane < WPB ? s_crow[wave & 1][lane] : -5;
+    float v = lane < WPB ? s_cval[wave & 1][lane] : 0.f;
 #pragma unroll
     for (int o = 1; o < WPB; o <<= 1) {
       const float vo = __shfl_up_sync(kFull, v, o, WPB);
@@ -1004,12 +1029,14 @@ __global__ void __launch_bounds__(256) mp_spmv_warp_kernel(MpArgs a) {
       __stcg(py, __ldcg(py) + v);
     }
     if (lane == WPB - 1) {
-      a.carry_row[blockIdx.x] = row;
-      a.carry_val[blockIdx.x] = v;
+      a.carry_row[(size_t)wave * a.num_ctas + blockIdx.x] = row;
+      a.carry_val[(size_t)wave * a.num_ctas + blockIdx.x] = v;
     }
   }
-  if (!cta_ticket(a, &s_last)) return;
-  last_cta_fixup<256>(a, s_wv, s_wf, s_incl);
+  }  // waves
+  // rows split between CTAs, all waves at once (a wave's rows are never
+  // touched by a later wave, and the slots of all waves are in row order)
+  if (cta_ticket(a, &s_last)) last_cta_fixup<256>(a, nwaves * a.num_ctas, s_wv, s_wf, s_incl);
 }
 
 // Warp-worker expand: the tile of every atom from the same row marks, then
@@ -1024,15 +1051,23 @@ __global__ void __launch_bounds__(256) mp_expand_warp_kernel(MpArgs a) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int w = blockIdx.x * WPB + warp;
   WarpScratch<IPT>& sc = sc_all[warp];
-  const int2* sp = a.splits + (size_t)w * (a.tiles_per_cta + 1);
-  const int32_t* sm = XB ? a.split_m + (size_t)w * (a.tiles_per_cta + 1) : nullptr;
-  int2 c0 = __ldg(sp);
-  const int2 e1 = __ldg(sp + a.tiles_per_cta);
-  const int64_t share = (int64_t)(e1.x - c0.x) + (e1.y - c0.y);
-  const int ntiles = (int)((share + a.items_per_tile - 1) / a.items_per_tile);
   if (lane < IPT) sc.bits[lane] = 0u;
   __syncwarp();
   const int s0 = lane * IPT;
+  const int nwaves = a.waves ? a.num_waves : 1;
+  for (int wave = 0; wave < nwaves; ++wave) {
+  int64_t ebase = 0;
+  int tpc = a.tiles_per_cta;
+  if (a.waves) {
+    ebase = a.waves[wave].entry_base;
+    tpc = a.waves[wave].tpc;
+  }
+  const int2* sp = a.splits + (size_t)ebase + (size_t)w * (tpc + 1);
+  const int32_t* sm = XB ? a.split_m + (size_t)ebase + (size_t)w * (tpc + 1) : nullptr;
+  int2 c0 = __ldg(sp);
+  const int2 e1 = __ldg(sp + tpc);
+  const int64_t share = (int64_t)(e1.x - c0.x) + (e1.y - c0.y);
+  const int ntiles = (int)((share + a.items_per_tile - 1) / a.items_per_tile);
   for (int k = 0; k < ntiles; ++k) {
     const int2 c1 = __ldg(sp + k + 1);
     const int nrows = c1.x - c0.x, nnz = c1.y - c0.y, j0 = c0.y, off = j0 & 3;
@@ -1087,6 +1122,7 @@ __global__ void __launch_bounds__(256) mp_expand_warp_kernel(MpArgs a) {
     __syncwarp();
     c0 = c1;
   }
+  }  // waves
 }
 
 // ---------------------------------------------------------- thread-mapped --

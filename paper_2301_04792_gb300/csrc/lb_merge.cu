@@ -1,6 +1,7 @@
 // Merge-path split tables and kernel launches, plus the thread-mapped and
 // group-mapped launchers.
 #include <algorithm>
+#include <vector>
 
 #include "lb_internal.h"
 #include "lb_kernels.cuh"
@@ -11,6 +12,9 @@ void MpTable::release() {
   cudaFree(splits);
   cudaFree(d_diag);
   cudaFree(split_m);
+  cudaFree(d_waves);
+  d_waves = nullptr;
+  num_waves = 1;
   cudaFree(carry_val);
   cudaFree(carry_row);
   cudaFree(ticket);
@@ -204,6 +208,41 @@ __global__ void mp_splits_kernel(const int32_t* __restrict__ rp, int32_t R, int6
   diag[e] = d;
 }
 
+// Splits of a waved table: entry e belongs to wave v (largest v with
+// entry_base[v] <= e); inside the wave, worker w = local / (tpc+1) owns the
+// items [floor(w*I/P), floor((w+1)*I/P)) of the wave's I items, tile k starts
+// k*items_per_tile in.
+__global__ void mp_splits_waves_kernel(const int32_t* __restrict__ rp, int32_t R, int64_t N,
+                                       const int64_t* __restrict__ wave_begin, const lbk::WaveDesc* __restrict__ wd,
+                                       int num_waves, int workers, int ipt_items, int64_t entries, int2* out,
+                                       int64_t* diag) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= entries) return;
+  int lo = 0, hi = num_waves - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (wd[mid].entry_base <= e) lo = mid;
+    else hi = mid - 1;
+  }
+  const int v = lo;
+  const int64_t local = e - wd[v].entry_base;
+  const int tpc = wd[v].tpc;
+  const int64_t w = local / (tpc + 1), k = local % (tpc + 1);
+  const int64_t items = wave_begin[v + 1] - wave_begin[v];
+  const int64_t b = wave_begin[v] + w * items / workers, en = wave_begin[v] + (w + 1) * items / workers;
+  const int64_t d0 = b + k * (int64_t)ipt_items;
+  const int64_t d = d0 < en ? d0 : en;
+  int64_t lo2 = d - N > 0 ? d - N : 0;
+  int64_t hi2 = d < R ? d : R;
+  while (lo2 < hi2) {
+    const int64_t mid = (lo2 + hi2) >> 1;
+    if ((int64_t)__ldg(rp + mid + 1) > d - mid - 1) hi2 = mid;
+    else lo2 = mid + 1;
+  }
+  out[e] = make_int2((int)lo2, (int)(d - lo2));
+  diag[e] = d;
+}
+
 // matrix holding each split's atom: largest m with nnz_base[m] <= j (over all matrices)
 __global__ void split_matrix_kernel(const int2* __restrict__ splits, int64_t entries,
                                     const int64_t* __restrict__ nnz_base, int num, int32_t* out) {
@@ -213,7 +252,8 @@ __global__ void split_matrix_kernel(const int2* __restrict__ splits, int64_t ent
 }
 
 lb_status_t build_mp_table(MpTable& t, const int32_t* rp, int32_t R, int64_t N, int ipt, int variant, int num_sms,
-                           int ctas_per_sm, const BatchBases* batch, cudaStream_t s) {
+                           int ctas_per_sm, const BatchBases* batch, cudaStream_t s, const int64_t* item_prefix,
+                           const int64_t* row_prefix, int num_mats, int wave_items) {
   t.release();
   if (!kernel_tma(ipt, false, false)) {
     set_error("items_per_thread must be 4, 8 or 16");
@@ -249,17 +289,74 @@ lb_status_t build_mp_table(MpTable& t, const int32_t* rp, int32_t R, int64_t N, 
     t.workers = t.grid;
   }
   t.entries = (int64_t)t.workers * (t.tiles_per_cta + 1);
+  // waves: runs of whole matrices, each big enough to give every worker a few
+  // tiles, so that the whole GPU works on about one wave at a time and the
+  // wave's dense vector stays in L2
+  std::vector<int64_t> wave_begin, wave_rows;  // diagonal and first row of every wave boundary
+  std::vector<lbk::WaveDesc> wd;
+  if (variant == 0 && item_prefix && row_prefix && num_mats > 1) {
+    const int64_t min_items =
+        wave_items > 0 ? (int64_t)wave_items
+                       : std::max<int64_t>((int64_t)4 << 20, (int64_t)t.workers * t.items_per_tile * 2);
+    wave_begin.push_back(0);
+    wave_rows.push_back(0);
+    for (int m = 1; m < num_mats; ++m) {
+      if (item_prefix[m] - wave_begin.back() >= min_items) {
+        wave_begin.push_back(item_prefix[m]);
+        wave_rows.push_back(row_prefix[m]);
+      }
+    }
+    // a short last wave joins the one before it
+    if (wave_begin.size() > 1 && t.items - wave_begin.back() < min_items / 2) {
+      wave_begin.pop_back();
+      wave_rows.pop_back();
+    }
+    wave_begin.push_back(t.items);
+    wave_rows.push_back(R);
+  }
+  const int nw = wave_begin.size() > 2 ? (int)wave_begin.size() - 1 : 1;
+  t.num_waves = nw;
+  if (nw > 1) {
+    int64_t base = 0;
+    int max_tpc = 1;
+    for (int v = 0; v < nw; ++v) {
+      const int64_t iv = wave_begin[v + 1] - wave_begin[v];
+      const int64_t share = (iv + t.workers - 1) / t.workers;
+      int64_t tpc = (share + t.items_per_tile - 1) / t.items_per_tile;
+      if (tpc < 1) tpc = 1;
+      wd.push_back(lbk::WaveDesc{base, (int32_t)tpc, (int32_t)wave_rows[v + 1]});
+      base += (int64_t)t.workers * (tpc + 1);
+      max_tpc = std::max(max_tpc, (int)tpc);
+    }
+    t.entries = base;
+    t.tiles_per_cta = max_tpc;
+  }
   LB_CUDA_TRY(cudaMalloc(&t.splits, sizeof(int2) * (size_t)t.entries));
   LB_CUDA_TRY(cudaMalloc(&t.d_diag, sizeof(int64_t) * (size_t)t.entries));
-  LB_CUDA_TRY(cudaMalloc(&t.carry_val, sizeof(float) * (size_t)t.workers));
-  LB_CUDA_TRY(cudaMalloc(&t.carry_row, sizeof(int32_t) * (size_t)t.workers));
-  LB_CUDA_TRY(cudaMalloc(&t.ticket, sizeof(unsigned)));
-  LB_CUDA_TRY(cudaMemsetAsync(t.ticket, 0, sizeof(unsigned), s));
+  LB_CUDA_TRY(cudaMalloc(&t.carry_val, sizeof(float) * (size_t)t.workers * nw));
+  LB_CUDA_TRY(cudaMalloc(&t.carry_row, sizeof(int32_t) * (size_t)t.workers * nw));
+  LB_CUDA_TRY(cudaMalloc(&t.ticket, sizeof(unsigned) * nw));
+  LB_CUDA_TRY(cudaMemsetAsync(t.ticket, 0, sizeof(unsigned) * nw, s));
   const int threads = 256;
   const unsigned blocks = (unsigned)((t.entries + threads - 1) / threads);
-  mp_splits_kernel<<<blocks, threads, 0, s>>>(rp, R, N, t.items, t.workers, t.tiles_per_cta, t.items_per_tile,
-                                              t.entries, t.splits, t.d_diag);
-  LB_CUDA_TRY(cudaGetLastError());
+  if (nw > 1) {
+    int64_t* d_begin = nullptr;
+    LB_CUDA_TRY(cudaMalloc(&t.d_waves, sizeof(lbk::WaveDesc) * nw));
+    LB_CUDA_TRY(cudaMalloc(&d_begin, sizeof(int64_t) * (nw + 1)));
+    LB_CUDA_TRY(cudaMemcpyAsync(t.d_waves, wd.data(), sizeof(lbk::WaveDesc) * nw, cudaMemcpyHostToDevice, s));
+    LB_CUDA_TRY(cudaMemcpyAsync(d_begin, wave_begin.data(), sizeof(int64_t) * (nw + 1), cudaMemcpyHostToDevice, s));
+    mp_splits_waves_kernel<<<blocks, threads, 0, s>>>(rp, R, N, d_begin, static_cast<lbk::WaveDesc*>(t.d_waves),
+                                                      nw, t.workers, t.items_per_tile, t.entries, t.splits,
+                                                      t.d_diag);
+    const cudaError_t e = cudaGetLastError();
+    cudaStreamSynchronize(s);
+    cudaFree(d_begin);
+    LB_CUDA_TRY(e);
+  } else {
+    mp_splits_kernel<<<blocks, threads, 0, s>>>(rp, R, N, t.items, t.workers, t.tiles_per_cta, t.items_per_tile,
+                                                t.entries, t.splits, t.d_diag);
+    LB_CUDA_TRY(cudaGetLastError());
+  }
   if (batch) {
     LB_CUDA_TRY(cudaMalloc(&t.split_m, sizeof(int32_t) * (size_t)t.entries));
     split_matrix_kernel<<<blocks, threads, 0, s>>>(t.splits, t.entries, batch->nnz_base, batch->num, t.split_m);
@@ -291,6 +388,8 @@ static lbk::MpArgs make_args(const MpTable& t, const SpmvCall& c) {
   a.carry_val = t.carry_val;
   a.carry_row = t.carry_row;
   a.ticket = t.ticket;
+  a.waves = static_cast<const lbk::WaveDesc*>(t.d_waves);
+  a.num_waves = t.num_waves;
   a.status = c.status;
   return a;
 }

@@ -197,7 +197,7 @@ class BatchPlan:
     """One persistent merge-path plan over a batch of CSR matrices."""
 
     def __init__(self, rows, cols, nnz, rp_cat: torch.Tensor, items_per_thread: int = 0, ctas_per_sm: int = 0,
-                 mp_variant: int = 0, stream=None):
+                 mp_variant: int = 0, wave_items: int = 0, stream=None):
         self._lib = _lib.load()
         _need(rp_cat, torch.int32, "rp_cat")
         self.rows = np.ascontiguousarray(rows, dtype=np.int32)
@@ -212,7 +212,7 @@ class BatchPlan:
         self.total_cols = int(self.cols.sum())
         self.total_nnz = int(self.nnz.sum())
         opts = PlanOpts(items_per_thread=int(items_per_thread), ctas_per_sm=int(ctas_per_sm),
-                        mp_variant=int(mp_variant))
+                        mp_variant=int(mp_variant), wave_items=int(wave_items))
         h = ctypes.c_void_p()
         check(self._lib.lb_batch_plan(ctypes.byref(h), self.rows.shape[0], self.rows.ctypes.data_as(ctypes.c_void_p),
                                       self.cols.ctypes.data_as(ctypes.c_void_p),
