@@ -52,7 +52,7 @@ struct MpTable {
   void* d_waves = nullptr;    // lbk::WaveDesc[num_waves] when num_waves > 1
   float* carry_val = nullptr; // [num_waves x grid]
   int32_t* carry_row = nullptr;
-  unsigned* ticket = nullptr; // [num_waves]
+  unsigned* ticket = nullptr; // [2]: fix-up ticket, work-unit counter
   void release();
 };
 

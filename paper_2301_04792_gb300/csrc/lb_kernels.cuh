@@ -197,9 +197,9 @@ struct MpArgs {
   int64_t num_atoms;         // length of the atom arrays (bounds of vector loads)
   const WaveDesc* waves;    // batched tables: the waves in order; nullptr = one wave
   int num_waves;
-  float* carry_val;         // [num_waves x num_ctas]
+  float* carry_val;         // [num_waves x num_ctas], one slot per work unit
   int32_t* carry_row;       // [num_waves x num_ctas]
-  unsigned* ticket;         // zero between launches
+  unsigned* ticket;         // [0] fix-up ticket, [1] next work unit; both zero between launches
   int* status;
   // expand kernels
   const float* dy;          // dvals: upstream gradient per tile
@@ -301,7 +301,10 @@ __device__ __forceinline__ void last_cta_fixup(const MpArgs& a, int num_slots, f
     run_in = total;
     __syncthreads();
   }
-  if (threadIdx.x == 0) *a.ticket = 0u;
+  if (threadIdx.x == 0) {
+    a.ticket[0] = 0u;
+    a.ticket[1] = 0u;
+  }
 }
 
 // Ticket that elects the last CTA to finish, after every thread of this CTA
@@ -877,10 +880,10 @@ __global__ void __launch_bounds__(256, IPT <= 8 ? 4 : 2) mp_spmv_warp_kernel(MpA
   __shared__ int s_wf[WPB];
   __shared__ float s_incl[256];
   __shared__ int s_last;
-  __shared__ int s_crow[2][WPB];  // by wave parity: a warp may write its next wave's carry while
-  __shared__ float s_cval[2][WPB];  // warp 0 still reads this wave's
+  __shared__ int s_crow[2][WPB];  // by unit parity: a warp may write its next unit's carry while
+  __shared__ float s_cval[2][WPB];  // warp 0 still reads this unit's
+  __shared__ int s_unit[2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int w = blockIdx.x * WPB + warp;
   WarpScratch<IPT>& sc = sc_all[warp];
   const AtomView& at = a.atoms;
   const int32_t* vsrc = PERM ? at.perm : reinterpret_cast<const int32_t*>(at.val);
@@ -888,12 +891,23 @@ __global__ void __launch_bounds__(256, IPT <= 8 ? 4 : 2) mp_spmv_warp_kernel(MpA
   if (lane < IPT) sc.bits[lane] = 0u;
   __syncwarp();
   const int s0 = lane * IPT;
-  const int nwaves = a.waves ? a.num_waves : 1;
-  for (int wave = 0; wave < nwaves; ++wave) {
+  // tables in waves come from batches: the forward (XB) or the transposed one
+  // of dx (PERM); the single-matrix forward drops the wave logic
+  constexpr bool kMayWave = XB || PERM;
+  const int nwaves = kMayWave && a.waves ? a.num_waves : 1;
+  const int nunits = nwaves * a.num_ctas;
+  // Work unit u = the 8 consecutive warp shares (u mod num_ctas) * 8 + warp of
+  // wave u / num_ctas.  One wave: unit blockIdx.x only.  Several waves: units
+  // are taken in order from a counter, so the CTAs work on the earliest open
+  // shares and the data in use spans about one wave however long the batch.
+  int u = blockIdx.x;
+  for (int it = 0; u < nunits; ++it) {
+  const int wave = u / a.num_ctas;
+  const int w = (u - wave * a.num_ctas) * WPB + warp;
   int64_t ebase = 0;
   int tpc = a.tiles_per_cta;
   int row_end = a.num_tiles;
-  if (a.waves) {
+  if (kMayWave && a.waves) {
     ebase = a.waves[wave].entry_base;
     tpc = a.waves[wave].tpc;
     row_end = a.waves[wave].row_end;
@@ -1010,13 +1024,14 @@ __global__ void __launch_bounds__(256, IPT <= 8 ? 4 : 2) mp_spmv_warp_kernel(MpA
   // by row; a run that a later warp of this CTA closed is added to its row,
   // the run left open by the last warp becomes the CTA's carry-out.
   if (lane == 0) {
-    s_crow[wave & 1][warp] = c0.x < row_end ? c0.x : -1;
-    s_cval[wave & 1][warp] = carry;
+    s_crow[it & 1][warp] = c0.x < row_end ? c0.x : -1;
+    s_cval[it & 1][warp] = carry;
   }
+  if (threadIdx.x == 0) s_unit[it & 1] = nwaves > 1 ? (int)gridDim.x + (int)atomicAdd(a.ticket + 1, 1u) : nunits;
   __syncthreads();
   if (warp == 0) {
-    const int row = lane < WPB ? s_crow[wave & 1][lane] : -5;
-    float v = lane < WPB ? s_cval[wave & 1][lane] : 0.f;
+    const int row = lane < WPB ? s_crow[it & 1][lane] : -5;
+    float v = lane < WPB ? s_cval[it & 1][lane] : 0.f;
 #pragma unroll
     for (int o = 1; o < WPB; o <<= 1) {
       const float vo = __shfl_up_sync(kFull, v, o, WPB);
@@ -1029,11 +1044,12 @@ __global__ void __launch_bounds__(256, IPT <= 8 ? 4 : 2) mp_spmv_warp_kernel(MpA
       __stcg(py, __ldcg(py) + v);
     }
     if (lane == WPB - 1) {
-      a.carry_row[(size_t)wave * a.num_ctas + blockIdx.x] = row;
-      a.carry_val[(size_t)wave * a.num_ctas + blockIdx.x] = v;
+      a.carry_row[u] = row;
+      a.carry_val[u] = v;
     }
   }
-  }  // waves
+  u = s_unit[it & 1];
+  }  // units
   // rows split between CTAs, all waves at once (a wave's rows are never
   // touched by a later wave, and the slots of all waves are in row order)
   if (cta_ticket(a, &s_last)) last_cta_fixup<256>(a, nwaves * a.num_ctas, s_wv, s_wf, s_incl);
@@ -1048,14 +1064,20 @@ template <int IPT, bool XB, bool DVALS>
 __global__ void __launch_bounds__(256) mp_expand_warp_kernel(MpArgs a) {
   constexpr int WPB = 8;
   __shared__ WarpScratch<IPT> sc_all[WPB];
+  __shared__ int s_unit[2];
+  __shared__ int s_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int w = blockIdx.x * WPB + warp;
   WarpScratch<IPT>& sc = sc_all[warp];
   if (lane < IPT) sc.bits[lane] = 0u;
   __syncwarp();
   const int s0 = lane * IPT;
   const int nwaves = a.waves ? a.num_waves : 1;
-  for (int wave = 0; wave < nwaves; ++wave) {
+  const int nunits = nwaves * a.num_ctas;
+  // work units as in mp_spmv_warp_kernel: several waves take them in order
+  int u = blockIdx.x;
+  for (int it = 0; u < nunits; ++it) {
+  const int wave = u / a.num_ctas;
+  const int w = (u - wave * a.num_ctas) * WPB + warp;
   int64_t ebase = 0;
   int tpc = a.tiles_per_cta;
   if (a.waves) {
@@ -1122,7 +1144,19 @@ __global__ void __launch_bounds__(256) mp_expand_warp_kernel(MpArgs a) {
     __syncwarp();
     c0 = c1;
   }
-  }  // waves
+  if (nwaves > 1) {
+    if (threadIdx.x == 0) s_unit[it & 1] = (int)gridDim.x + (int)atomicAdd(a.ticket + 1, 1u);
+    __syncthreads();
+    u = s_unit[it & 1];
+  } else {
+    u = nunits;
+  }
+  }  // units
+  // the last CTA to finish resets the unit counter for the next launch
+  if (nwaves > 1 && cta_ticket(a, &s_last) && threadIdx.x == 0) {
+    a.ticket[0] = 0u;
+    a.ticket[1] = 0u;
+  }
 }
 
 // ---------------------------------------------------------- thread-mapped --

@@ -335,8 +335,8 @@ lb_status_t build_mp_table(MpTable& t, const int32_t* rp, int32_t R, int64_t N, 
   LB_CUDA_TRY(cudaMalloc(&t.d_diag, sizeof(int64_t) * (size_t)t.entries));
   LB_CUDA_TRY(cudaMalloc(&t.carry_val, sizeof(float) * (size_t)t.workers * nw));
   LB_CUDA_TRY(cudaMalloc(&t.carry_row, sizeof(int32_t) * (size_t)t.workers * nw));
-  LB_CUDA_TRY(cudaMalloc(&t.ticket, sizeof(unsigned) * nw));
-  LB_CUDA_TRY(cudaMemsetAsync(t.ticket, 0, sizeof(unsigned) * nw, s));
+  LB_CUDA_TRY(cudaMalloc(&t.ticket, sizeof(unsigned) * 2));
+  LB_CUDA_TRY(cudaMemsetAsync(t.ticket, 0, sizeof(unsigned) * 2, s));
   const int threads = 256;
   const unsigned blocks = (unsigned)((t.entries + threads - 1) / threads);
   if (nw > 1) {
@@ -402,6 +402,10 @@ lb_status_t launch_mp_spmv(const MpTable& t, const SpmvCall& c, cudaStream_t s) 
   if (t.items == 0) return LB_OK;
   if (c.batch && !t.split_m) {
     set_error("batched launch on a table without matrix indices");
+    return LB_ERR_INVALID_ARG;
+  }
+  if (t.num_waves > 1 && !c.batch && !c.perm) {  // the forward kernels walk waves only when batched
+    set_error("a table in waves needs a batched or transposed launch");
     return LB_ERR_INVALID_ARG;
   }
   lbk::MpArgs a = make_args(t, c);

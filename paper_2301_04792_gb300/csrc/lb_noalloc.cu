@@ -121,8 +121,8 @@ lb_status_t lb_spmv_noalloc(const int32_t* tile_offsets, int32_t num_tiles, int3
   }
   unsigned char* base = d->base;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // the ticket must start at zero; the array keeps the previous call's contents
-  LB_CUDA_TRY(cudaMemsetAsync(base, 0, sizeof(unsigned), s));
+  // the ticket and unit counter must start at zero; the array keeps the previous call's contents
+  LB_CUDA_TRY(cudaMemsetAsync(base, 0, 2 * sizeof(unsigned), s));
   int2* splits = reinterpret_cast<int2*>(base + off_splits);
   int64_t* diag = reinterpret_cast<int64_t*>(base + off_diag);
   const unsigned sblocks = (unsigned)((entries + 255) / 256);
