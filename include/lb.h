@@ -225,6 +225,78 @@ lb_status_t lb_status(lb_plan_t plan, void* stream);
 lb_status_t lb_spmv_noalloc(const int32_t* tile_offsets, int32_t num_tiles, int32_t num_atoms,
                             const int32_t* col_idx, const float* vals, const float* x, float* y, void* stream);
 
+/* ------------------------------------------------------------- autotuner -- */
+/*
+ * Measured choice of schedule and tile size for one matrix (no counterpart in
+ * the paper's code: Sec. 6.2 gives only a size heuristic, which serves here as
+ * the prior and is timed among the candidates).  Every candidate below is
+ * planned, launched once untimed, then timed with CUDA events on `stream` over
+ * the caller's real col_idx / vals / x; the fastest median wins (ties go to the
+ * earlier candidate, the heuristic's choice first).
+ *
+ * Candidate families (bits of lb_tune_opts_t.families; 0 = all):
+ *   LB_TUNE_MP_WARP  merge-path, warp workers, items_per_thread 4, 8, 16
+ *   LB_TUNE_MP_CTA   merge-path, CTA workers: per-thread search (variant 1) and
+ *                    bulk-copy ring (variant 2, only for 16-byte aligned buffers),
+ *                    items_per_thread 4 and 8
+ *   LB_TUNE_THREAD   thread-mapped
+ *   LB_TUNE_GROUP    group-mapped with groups of 4, 8, 16, 32 (warp-mapped), 64,
+ *                    128 and 256 (block-mapped) threads
+ */
+#define LB_TUNE_MAX_CANDIDATES 20
+#define LB_TUNE_MP_WARP 1
+#define LB_TUNE_MP_CTA 2
+#define LB_TUNE_THREAD 4
+#define LB_TUNE_GROUP 8
+typedef struct lb_tune_opts_t {
+  int32_t num_cols;       /* columns of A, > 0 when num_atoms > 0 (bytes of x, group plans) */
+  int32_t reps;           /* timed launches of each candidate that survives its first (default 5) */
+  float prune_factor;     /* a candidate whose first timed launch takes more than prune_factor x the
+                             best median so far is not timed again (default 3) */
+  int32_t cold_l2;        /* nonzero: overwrite a scratch of twice the L2 size before every timed launch
+                             (inputs smaller than L2 are then read from HBM, as in a cold call) */
+  int32_t no_cache;       /* nonzero: neither read nor update the process-wide cache */
+  int32_t families;       /* bit mask of LB_TUNE_* candidate families; 0 = all */
+  int32_t reserved[2];
+} lb_tune_opts_t;
+typedef struct lb_tune_candidate_t {
+  int32_t schedule;         /* lb_schedule_t */
+  int32_t items_per_thread; /* merge-path */
+  int32_t group_size;       /* group-mapped schedules (32 warp-, 256 block-mapped) */
+  int32_t mp_variant;       /* merge-path worker variant */
+  float ms;                 /* median time of one lb_spmv in milliseconds (the single time if pruned) */
+  float gbps;               /* algorithmic bytes (8 nnz + 4 (rows + 1) + 4 cols + 4 rows) / ms */
+  int32_t reps;             /* timed launches */
+  int32_t status;           /* lb_status_t of planning or running it; other fields are 0 unless LB_OK */
+} lb_tune_candidate_t;
+typedef struct lb_tune_result_t {
+  int32_t num_candidates;   /* entries of candidates[] filled */
+  int32_t best;             /* index of the winner in candidates[] */
+  int32_t heuristic;        /* index of the Sec. 6.2 heuristic's choice (merge-path items_per_thread 8 or
+                               thread-mapped) in candidates[] */
+  int32_t from_cache;       /* 1: result taken from the process-wide cache, nothing was timed */
+  int32_t best_schedule;    /* lb_schedule_t of the winner */
+  lb_plan_opts_t best_opts; /* options that rebuild the winner with lb_plan_ex(best_schedule) */
+  lb_tune_candidate_t candidates[LB_TUNE_MAX_CANDIDATES];
+} lb_tune_result_t;
+/*
+ * Times the candidates for y = A x on the tile set `tile_offsets` (device,
+ * int32 [num_tiles + 1]) with col_idx, vals (device [num_atoms]) and x (device
+ * [opts->num_cols]), writes the table to *result (host) and, when out_plan is
+ * not NULL, a plan built with the winner to *out_plan (the caller destroys it).
+ * On return y (device [num_tiles], caller-owned) holds A x computed by the
+ * winner.  The process-wide cache is keyed by device, sizes and a fingerprint
+ * of tile_offsets and of 4096 evenly spaced col_idx entries; a hit skips the
+ * timing.  Allocates (plans, the cold-L2 scratch) and synchronises `stream`.
+ * Errors: LB_ERR_INVALID_ARG (NULL result, negative sizes, NULL buffers with
+ * num_atoms > 0, num_cols < 1 with num_atoms > 0), LB_ERR_CUDA, LB_ERR_OOM;
+ * a candidate that fails is recorded with its status and skipped.
+ */
+lb_status_t lb_autotune(const int32_t* tile_offsets, int32_t num_tiles, int32_t num_atoms, const int32_t* col_idx,
+                        const float* vals, const float* x, float* y, const lb_tune_opts_t* opts,
+                        lb_tune_result_t* result, lb_plan_t* out_plan, void* stream);
+/* Empties the autotuner's process-wide cache. */
+void lb_autotune_cache_clear(void);
 /* -------------------------------------------------------------- batching -- */
 
 /*

@@ -8,8 +8,8 @@ differentiable backward and a batched persistent form.  The compute lives in
 ``liblb.so`` (C ABI ``include/lb.h``); this package marshals arguments.
 """
 from .buildlib import build  # noqa: F401
-from .lb import (BatchPlan, LBBatchSpMV, LBSpMV, Plan, Schedule, batch_spmv, heuristic_schedule,  # noqa: F401
-                 merge_diagonals, spmv)
+from .lb import (BatchPlan, LBBatchSpMV, LBSpMV, Plan, Schedule, autotune, autotune_cache_clear,  # noqa: F401
+                 batch_spmv, heuristic_schedule, merge_diagonals, spmv)
 
 __all__ = ["build", "Plan", "BatchPlan", "Schedule", "LBSpMV", "LBBatchSpMV", "spmv", "batch_spmv",
-           "heuristic_schedule", "merge_diagonals"]
+           "heuristic_schedule", "merge_diagonals", "autotune", "autotune_cache_clear"]

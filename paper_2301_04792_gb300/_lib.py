@@ -40,6 +40,28 @@ class PlanInfo(ctypes.Structure):
                 ("has_transpose", ctypes.c_int32)]
 
 
+TUNE_MAX_CANDIDATES = 20
+TUNE_MP_WARP, TUNE_MP_CTA, TUNE_THREAD, TUNE_GROUP = 1, 2, 4, 8
+
+
+class TuneOpts(ctypes.Structure):
+    _fields_ = [("num_cols", ctypes.c_int32), ("reps", ctypes.c_int32), ("prune_factor", ctypes.c_float),
+                ("cold_l2", ctypes.c_int32), ("no_cache", ctypes.c_int32), ("families", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
+
+
+class TuneCandidate(ctypes.Structure):
+    _fields_ = [("schedule", ctypes.c_int32), ("items_per_thread", ctypes.c_int32), ("group_size", ctypes.c_int32),
+                ("mp_variant", ctypes.c_int32), ("ms", ctypes.c_float), ("gbps", ctypes.c_float),
+                ("reps", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("num_candidates", ctypes.c_int32), ("best", ctypes.c_int32), ("heuristic", ctypes.c_int32),
+                ("from_cache", ctypes.c_int32), ("best_schedule", ctypes.c_int32), ("best_opts", PlanOpts),
+                ("candidates", TuneCandidate * TUNE_MAX_CANDIDATES)]
+
+
 # name -> (restype, argtypes); the declarations of include/lb.h
 VP, I32, I64, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
 PLANP = ctypes.POINTER(ctypes.c_void_p)
@@ -56,6 +78,9 @@ SIGNATURES = {
     "lb_atom_tiles": (I32, [VP, VP, VP]),
     "lb_spmv_noalloc": (I32, [VP, I32, I32, VP, VP, VP, VP, VP]),
     "lb_status": (I32, [VP, VP]),
+    "lb_autotune": (I32, [VP, I32, I32, VP, VP, VP, VP, ctypes.POINTER(TuneOpts), ctypes.POINTER(TuneResult), PLANP,
+                          VP]),
+    "lb_autotune_cache_clear": (None, []),
     "lb_batch_plan": (I32, [PLANP, I32, VP, VP, VP, VP, ctypes.POINTER(PlanOpts), VP]),
     "lb_batch_spmv": (I32, [VP, VP, VP, VP, VP, VP]),
     "lb_batch_prepare_backward": (I32, [VP, VP, VP]),

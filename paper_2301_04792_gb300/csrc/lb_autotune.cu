@@ -1,0 +1,289 @@
+// Autotuner: the schedule and tile size of one matrix chosen by timing every
+// candidate on the caller's own data.  The paper fixes the choice by a size
+// rule (Sec. 6.2, alpha = 500 rows or columns, beta = 10,000 nonzeros); that
+// rule is kept as the prior -- its pick is timed first and wins ties -- and
+// the measurement decides.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "lb_internal.h"
+
+using namespace lbh;
+
+namespace {
+
+// splitmix64 output function (Steele, Lea and Flood, "Fast splittable
+// pseudorandom number generators", OOPSLA 2014): a bijective 64-bit mixer.
+__host__ __device__ inline uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+
+// Order-independent fingerprint of the tile set and of a sample of the column
+// indices: XOR over entries of mix64(position, value).
+__global__ void fingerprint_kernel(const int32_t* __restrict__ rp, int32_t R, const int32_t* __restrict__ ci,
+                                   int64_t N, int64_t stride, int32_t samples, unsigned long long* out) {
+  uint64_t h = 0;
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= R; i += nthreads)
+    h ^= mix64(((uint64_t)i << 32) ^ (uint32_t)rp[i]);
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < samples; q += nthreads) {
+    const int64_t k = q * stride;
+    if (k < N) h ^= mix64(0x5bd1e995ULL * (uint64_t)(k + 1) ^ ((uint64_t)(uint32_t)ci[k] << 17));
+  }
+  for (int o = 16; o > 0; o >>= 1) h ^= __shfl_xor_sync(0xffffffffu, h, o);
+  if ((threadIdx.x & 31) == 0 && h) atomicXor(out, (unsigned long long)h);
+}
+
+struct Candidate {
+  lb_schedule_t schedule;
+  int ipt, group, variant;
+};
+
+using Key = std::tuple<int, int32_t, int32_t, int32_t, uint64_t, int32_t, int32_t>;
+std::mutex g_cache_mu;
+std::map<Key, lb_tune_result_t> g_cache;
+
+std::vector<Candidate> candidate_list(lb_schedule_t prior, int families, bool aligned) {
+  std::vector<Candidate> v;
+  // the heuristic's pick first, so that it wins ties
+  if (prior == LB_THREAD_MAPPED && (families & LB_TUNE_THREAD)) v.push_back({LB_THREAD_MAPPED, 0, 0, 0});
+  if (families & LB_TUNE_MP_WARP)
+    for (int ipt : {8, 4, 16}) v.push_back({LB_MERGE_PATH, ipt, 0, 0});
+  if (families & LB_TUNE_MP_CTA) {
+    for (int ipt : {4, 8}) v.push_back({LB_MERGE_PATH, ipt, 0, 1});
+    if (aligned)
+      for (int ipt : {4, 8}) v.push_back({LB_MERGE_PATH, ipt, 0, 2});
+  }
+  if (prior != LB_THREAD_MAPPED && (families & LB_TUNE_THREAD)) v.push_back({LB_THREAD_MAPPED, 0, 0, 0});
+  if (families & LB_TUNE_GROUP) {
+    for (int g : {4, 8, 16}) v.push_back({LB_GROUP_MAPPED, 0, g, 0});
+    v.push_back({LB_WARP_MAPPED, 0, 32, 0});
+    for (int g : {64, 128}) v.push_back({LB_GROUP_MAPPED, 0, g, 0});
+    v.push_back({LB_BLOCK_MAPPED, 0, 256, 0});
+  }
+  return v;
+}
+
+lb_plan_opts_t opts_of(const Candidate& c, int32_t num_cols) {
+  lb_plan_opts_t o{};
+  o.num_cols = num_cols;
+  o.items_per_thread = c.ipt ? c.ipt : 8;
+  o.group_size = c.group;
+  o.mp_variant = c.variant;
+  return o;
+}
+
+// Events and the optional cold-L2 scratch of one tuning call.
+struct Timer {
+  cudaStream_t s;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  void* flush = nullptr;
+  size_t flush_bytes = 0;
+  int flush_round = 0;
+  ~Timer() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (flush) cudaFree(flush);
+  }
+  lb_status_t init(bool cold_l2, int dev) {
+    LB_CUDA_TRY(cudaEventCreate(&e0));
+    LB_CUDA_TRY(cudaEventCreate(&e1));
+    if (cold_l2) {
+      int l2 = 0;
+      LB_CUDA_TRY(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+      flush_bytes = (size_t)std::max(l2, 1 << 20) * 2;
+      LB_CUDA_TRY(cudaMalloc(&flush, flush_bytes));
+    }
+    return LB_OK;
+  }
+  // one launch of the plan, timed on the stream; the scratch is rewritten first
+  lb_status_t once(lb_plan_t p, const int32_t* ci, const float* v, const float* x, float* y, float* ms) {
+    if (flush) LB_CUDA_TRY(cudaMemsetAsync(flush, ++flush_round & 0xff, flush_bytes, s));
+    LB_CUDA_TRY(cudaEventRecord(e0, s));
+    LB_TRY(lb_spmv(p, ci, v, x, y, s));
+    LB_CUDA_TRY(cudaEventRecord(e1, s));
+    LB_CUDA_TRY(cudaEventSynchronize(e1));
+    LB_CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
+    return LB_OK;
+  }
+};
+
+lb_status_t run_candidate(const Candidate& c, const int32_t* rp, int32_t R, int32_t N, int32_t C,
+                          const int32_t* ci, const float* v, const float* x, float* y, int reps, float prune_ms,
+                          Timer& t, lb_tune_candidate_t* out) {
+  const lb_plan_opts_t o = opts_of(c, C);
+  lb_plan_t p = nullptr;
+  LB_TRY(lb_plan_ex(&p, rp, R, N, c.schedule, &o, t.s));
+  struct Guard {
+    lb_plan_t p;
+    ~Guard() { lb_plan_destroy(p); }
+  } guard{p};
+  LB_TRY(lb_spmv(p, ci, v, x, y, t.s));  // untimed: first-use costs (module load, cold TLB)
+  float first = 0.f;
+  LB_TRY(t.once(p, ci, v, x, y, &first));
+  std::vector<float> ms{first};
+  if (!(first > prune_ms)) {
+    for (int r = 1; r < reps; ++r) {
+      float m = 0.f;
+      LB_TRY(t.once(p, ci, v, x, y, &m));
+      ms.push_back(m);
+    }
+  }
+  std::sort(ms.begin(), ms.end());
+  out->ms = ms[ms.size() / 2];
+  out->reps = (int32_t)ms.size();
+  return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lb_autotune_cache_clear(void) {
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  g_cache.clear();
+}
+
+lb_status_t lb_autotune(const int32_t* tile_offsets, int32_t num_tiles, int32_t num_atoms, const int32_t* col_idx,
+                        const float* vals, const float* x, float* y, const lb_tune_opts_t* opts,
+                        lb_tune_result_t* result, lb_plan_t* out_plan, void* stream) {
+  if (out_plan) *out_plan = nullptr;
+  if (!result || !opts) {
+    set_error("lb_autotune: result and opts must not be NULL");
+    return LB_ERR_INVALID_ARG;
+  }
+  std::memset(result, 0, sizeof(*result));
+  const int32_t C = opts->num_cols;
+  if (num_tiles < 0 || num_atoms < 0 || (num_tiles == 0 && num_atoms != 0) || (num_tiles > 0 && !tile_offsets) ||
+      (num_tiles > 0 && !y) || (num_atoms > 0 && (!col_idx || !vals || !x || C < 1)) || C < 0 ||
+      opts->reps < 0 || opts->prune_factor < 0.f) {
+    set_error("lb_autotune: need num_tiles, num_atoms >= 0, buffers for nonzero sizes and num_cols >= 1");
+    return LB_ERR_INVALID_ARG;
+  }
+  const int reps = opts->reps ? opts->reps : 5;
+  const float prune = opts->prune_factor > 0.f ? opts->prune_factor : 3.f;
+  const int families = opts->families ? opts->families : (LB_TUNE_MP_WARP | LB_TUNE_MP_CTA | LB_TUNE_THREAD |
+                                                           LB_TUNE_GROUP);
+  const lb_schedule_t prior = lb_heuristic_schedule(num_tiles, C > 0 ? C : num_tiles, num_atoms);
+  const bool aligned = ((reinterpret_cast<uintptr_t>(col_idx) | reinterpret_cast<uintptr_t>(vals)) & 15u) == 0;
+  const std::vector<Candidate> cands = candidate_list(prior, families, aligned);
+  if (cands.empty()) {
+    set_error("lb_autotune: no candidate family selected");
+    return LB_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0;
+  LB_CUDA_TRY(cudaGetDevice(&dev));
+
+  // fingerprint for the cache
+  uint64_t fp = 0;
+  const bool use_cache = !opts->no_cache && num_tiles > 0;
+  if (use_cache) {
+    unsigned long long* d_fp = nullptr;
+    LB_CUDA_TRY(cudaMalloc(&d_fp, sizeof(unsigned long long)));
+    const int32_t samples = num_atoms > 0 ? (int32_t)std::min<int64_t>(4096, num_atoms) : 0;
+    const int64_t stride = samples > 0 ? std::max<int64_t>(1, num_atoms / samples) : 1;
+    const int64_t work = std::max<int64_t>((int64_t)num_tiles + 1, samples);
+    const unsigned blocks = (unsigned)std::min<int64_t>((work + 255) / 256, 4096);
+    cudaError_t e = cudaMemsetAsync(d_fp, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) {
+      fingerprint_kernel<<<blocks, 256, 0, s>>>(tile_offsets, num_tiles, col_idx, num_atoms, stride, samples, d_fp);
+      e = cudaGetLastError();
+    }
+    unsigned long long h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_fp, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_fp);
+    LB_CUDA_TRY(e);
+    fp = h;
+  }
+  const Key key{dev, num_tiles, num_atoms, C, fp, families, opts->cold_l2 ? 1 : 0};
+  bool hit = false;
+  if (use_cache) {
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end()) {
+      *result = it->second;
+      result->from_cache = 1;
+      hit = true;
+    }
+  }
+
+  if (!hit) {
+    Timer t;
+    t.s = s;
+    LB_TRY(t.init(opts->cold_l2 != 0, dev));
+    const double bytes = 8.0 * num_atoms + 4.0 * (num_tiles + 1) + 4.0 * C + 4.0 * num_tiles;
+    float best_ms = -1.f;
+    int best = -1, heur = -1;
+    const int n = (int)std::min<size_t>(cands.size(), LB_TUNE_MAX_CANDIDATES);
+    for (int i = 0; i < n; ++i) {
+      const Candidate& c = cands[i];
+      lb_tune_candidate_t& r = result->candidates[i];
+      r.schedule = c.schedule;
+      r.items_per_thread = c.ipt;
+      r.group_size = c.group;
+      r.mp_variant = c.variant;
+      if ((c.schedule == prior) && heur < 0 && (c.schedule != LB_MERGE_PATH || (c.ipt == 8 && c.variant == 0)))
+        heur = i;
+      if (num_tiles == 0) {
+        r.status = LB_OK;
+        if (best < 0) best = i;
+        continue;
+      }
+      const float prune_ms = best_ms > 0.f ? prune * best_ms : 3.0e38f;
+      r.status = run_candidate(c, tile_offsets, num_tiles, num_atoms, C, col_idx, vals, x, y, reps, prune_ms, t, &r);
+      if (r.status != LB_OK) {
+        // a candidate that cannot run here (e.g. out of memory for its tables) is skipped;
+        // a sticky device error ends the tuning
+        r.ms = 0.f;
+        r.reps = 0;
+        if (cudaPeekAtLastError() != cudaSuccess && cudaDeviceSynchronize() != cudaSuccess) return LB_ERR_CUDA;
+        continue;
+      }
+      r.gbps = r.ms > 0.f ? (float)(bytes / (r.ms * 1e-3) / 1e9) : 0.f;
+      if (best < 0 || r.ms < best_ms) {
+        best = i;
+        best_ms = r.ms;
+      }
+    }
+    if (best < 0) {
+      set_error("lb_autotune: no candidate ran");
+      return LB_ERR_CUDA;
+    }
+    result->num_candidates = n;
+    result->best = best;
+    result->heuristic = heur;
+    result->best_schedule = result->candidates[best].schedule;
+    result->best_opts = opts_of(cands[best], C);
+    if (use_cache) {
+      std::lock_guard<std::mutex> lock(g_cache_mu);
+      g_cache[key] = *result;
+    }
+  }
+
+  // the winner's plan; y = A x by it
+  lb_plan_t p = nullptr;
+  LB_TRY(lb_plan_ex(&p, tile_offsets, num_tiles, num_atoms, (lb_schedule_t)result->best_schedule,
+                    &result->best_opts, s));
+  lb_status_t st = lb_spmv(p, col_idx, vals, x, y, s);
+  if (st == LB_OK && cudaStreamSynchronize(s) != cudaSuccess) {
+    set_error("lb_autotune: final launch failed");
+    st = LB_ERR_CUDA;
+  }
+  if (st != LB_OK || !out_plan) {
+    lb_plan_destroy(p);
+  } else {
+    *out_plan = p;
+  }
+  return st;
+}
+
+}  // extern "C"

@@ -14,7 +14,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import PlanInfo, PlanOpts, check
+from ._lib import PlanInfo, PlanOpts, TuneOpts, TuneResult, check
 
 
 class Schedule(IntEnum):
@@ -104,6 +104,18 @@ class Plan:
               "lb_plan")
         self._h = h
 
+    @classmethod
+    def _adopt(cls, handle: ctypes.c_void_p, tile_offsets: torch.Tensor, num_atoms: int, num_cols: int) -> "Plan":
+        """Wraps a plan handle made by the library (the autotuner's winner)."""
+        self = cls.__new__(cls)
+        self._lib = _lib.load()
+        self.tile_offsets = tile_offsets
+        self.num_tiles = tile_offsets.numel() - 1
+        self.num_atoms = int(num_atoms)
+        self.num_cols = int(num_cols)
+        self._h = handle
+        return self
+
     # ------------------------------------------------------------------ util
     @property
     def handle(self):
@@ -191,6 +203,56 @@ class Plan:
             out = torch.empty(self.num_atoms, dtype=torch.int32, device=self.tile_offsets.device)
         check(self._lib.lb_atom_tiles(self.handle, _ptr(out), ctypes.c_void_p(_stream(stream))), "lb_atom_tiles")
         return out
+
+
+def _candidate_name(c) -> str:
+    s = Schedule(c.schedule)
+    if s == Schedule.MERGE_PATH:
+        return f"merge_path_ipt{c.items_per_thread}_v{c.mp_variant}"
+    if s == Schedule.GROUP_MAPPED:
+        return f"group_mapped_g{c.group_size}"
+    return s.name.lower()
+
+
+def autotune(tile_offsets: torch.Tensor, col_idx: torch.Tensor, vals: torch.Tensor, x: torch.Tensor,
+             num_cols: int | None = None, y: torch.Tensor | None = None, reps: int = 0, prune_factor: float = 0.0,
+             cold_l2: bool = False, use_cache: bool = True, families: int = 0, stream=None):
+    """Times every candidate schedule on this matrix (``lb_autotune``) and returns
+    ``(plan, report)``: the winner's Plan and a dict with the timed table.  ``y``
+    (allocated if None) holds A x by the winner afterwards (``report["y"]``)."""
+    lib = _lib.load()
+    _need(tile_offsets, torch.int32, "tile_offsets")
+    R = tile_offsets.numel() - 1
+    N = int(col_idx.numel())
+    _need(col_idx, torch.int32, "col_idx")
+    _need(vals, torch.float32, "vals", N)
+    _need(x, torch.float32, "x")
+    C = int(x.numel()) if num_cols is None else int(num_cols)
+    if y is None:
+        y = torch.empty(R, dtype=torch.float32, device=x.device)
+    _need(y, torch.float32, "y", R)
+    o = TuneOpts(num_cols=C, reps=int(reps), prune_factor=float(prune_factor), cold_l2=int(bool(cold_l2)),
+                 no_cache=int(not use_cache), families=int(families))
+    res = TuneResult()
+    h = ctypes.c_void_p()
+    check(lib.lb_autotune(_ptr(tile_offsets), R, N, _ptr(col_idx), _ptr(vals), _ptr(x), _ptr(y), ctypes.byref(o),
+                          ctypes.byref(res), ctypes.byref(h), ctypes.c_void_p(_stream(stream))), "lb_autotune")
+    cands = []
+    for i in range(res.num_candidates):
+        c = res.candidates[i]
+        cands.append({"name": _candidate_name(c), "schedule": Schedule(c.schedule).name.lower(),
+                      "items_per_thread": c.items_per_thread, "group_size": c.group_size,
+                      "mp_variant": c.mp_variant, "ms": c.ms, "gbps": c.gbps, "reps": c.reps, "status": c.status})
+    report = {"candidates": cands, "best": cands[res.best]["name"],
+              "heuristic": cands[res.heuristic]["name"] if res.heuristic >= 0 else None,
+              "from_cache": bool(res.from_cache), "best_schedule": Schedule(res.best_schedule).name.lower(),
+              "best_opts": {f: getattr(res.best_opts, f) for f, _ in PlanOpts._fields_ if f != "reserved"},
+              "y": y}
+    return Plan._adopt(h, tile_offsets, N, C), report
+
+
+def autotune_cache_clear():
+    _lib.load().lb_autotune_cache_clear()
 
 
 class BatchPlan:

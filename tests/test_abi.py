@@ -85,3 +85,24 @@ def test_merge_diagonals_rejects_bad_args(lib):
     assert lib.lb_merge_diagonals(-1, 1, 1, None, 0, ctypes.byref(n), ctypes.byref(t)) == 1
     assert lib.lb_merge_diagonals(10, 0, 1, None, 0, ctypes.byref(n), ctypes.byref(t)) == 1
     assert b"items" in lib.lb_last_error()
+
+
+def test_autotune_rejects_bad_args_before_any_launch(lib):
+    res = _lib.TuneResult()
+    opts = _lib.TuneOpts(num_cols=10)
+    plan = ctypes.c_void_p()
+    # no result / no opts
+    assert lib.lb_autotune(None, 0, 0, None, None, None, None, ctypes.byref(opts), None, None, None) == 1
+    assert lib.lb_autotune(None, 0, 0, None, None, None, None, None, ctypes.byref(res), None, None) == 1
+    # atoms without buffers, negative sizes, atoms without columns
+    assert lib.lb_autotune(None, 5, 10, None, None, None, None, ctypes.byref(opts), ctypes.byref(res),
+                           ctypes.byref(plan), None) == 1
+    assert lib.lb_autotune(None, -1, 0, None, None, None, None, ctypes.byref(opts), ctypes.byref(res), None,
+                           None) == 1
+    fake = ctypes.c_void_p(256)  # never dereferenced: the call is refused first
+    opts0 = _lib.TuneOpts(num_cols=0)
+    assert lib.lb_autotune(fake, 5, 10, fake, fake, fake, fake, ctypes.byref(opts0), ctypes.byref(res),
+                           None, None) == 1
+    assert b"num_cols" in lib.lb_last_error()
+    assert plan.value is None
+    assert ctypes.sizeof(_lib.TuneResult) == 5 * 4 + ctypes.sizeof(_lib.PlanOpts) + 20 * 32
