@@ -87,7 +87,12 @@ typedef struct lb_plan_opts_t {
   int32_t wave_items;       /* batches, warp workers: minimum rows + atoms of a wave (a run of whole
                                matrices shared out over all workers before the next run starts; keeps
                                the run's vectors in L2); 0 = max(4 Mi, 2 x workers x items_per_tile) */
-  int32_t reserved[1];
+  int32_t units_per_cta;    /* merge-path, warp workers: the rows + atoms are cut into this many equal
+                               work units per launched CTA (8 warp shares each), which the CTAs take in
+                               merge order from a counter, so a CTA that finishes early takes more work
+                               and the launch ends with less idle time (each unit ends in a CTA barrier,
+                               so more units pay off only where warps' times vary a lot, e.g. R-MAT);
+                               0 or 1 = one static unit per CTA */
 } lb_plan_opts_t;
 
 /* What a plan resolved to (for tests, the autotuner and reporting). */
@@ -235,7 +240,8 @@ lb_status_t lb_spmv_noalloc(const int32_t* tile_offsets, int32_t num_tiles, int3
  * earlier candidate, the heuristic's choice first).
  *
  * Candidate families (bits of lb_tune_opts_t.families; 0 = all):
- *   LB_TUNE_MP_WARP  merge-path, warp workers, items_per_thread 4, 8, 16
+ *   LB_TUNE_MP_WARP  merge-path, warp workers, items_per_thread 4, 8, 16 with one static unit
+ *                    per CTA, and items_per_thread 8 with 4 and 8 dynamic units per CTA
  *   LB_TUNE_MP_CTA   merge-path, CTA workers: per-thread search (variant 1) and
  *                    bulk-copy ring (variant 2, only for 16-byte aligned buffers),
  *                    items_per_thread 4 and 8
@@ -264,6 +270,7 @@ typedef struct lb_tune_candidate_t {
   int32_t items_per_thread; /* merge-path */
   int32_t group_size;       /* group-mapped schedules (32 warp-, 256 block-mapped) */
   int32_t mp_variant;       /* merge-path worker variant */
+  int32_t units_per_cta;    /* merge-path warp workers: work units per CTA */
   float ms;                 /* median time of one lb_spmv in milliseconds (the single time if pruned) */
   float gbps;               /* algorithmic bytes (8 nnz + 4 (rows + 1) + 4 cols + 4 rows) / ms */
   int32_t reps;             /* timed launches */

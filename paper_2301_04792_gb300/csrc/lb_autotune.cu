@@ -44,6 +44,7 @@ __global__ void fingerprint_kernel(const int32_t* __restrict__ rp, int32_t R, co
 struct Candidate {
   lb_schedule_t schedule;
   int ipt, group, variant;
+  int units = 1;  // merge-path warp workers: work units per CTA
 };
 
 using Key = std::tuple<int, int32_t, int32_t, int32_t, uint64_t, int32_t, int32_t>;
@@ -54,8 +55,10 @@ std::vector<Candidate> candidate_list(lb_schedule_t prior, int families, bool al
   std::vector<Candidate> v;
   // the heuristic's pick first, so that it wins ties
   if (prior == LB_THREAD_MAPPED && (families & LB_TUNE_THREAD)) v.push_back({LB_THREAD_MAPPED, 0, 0, 0});
-  if (families & LB_TUNE_MP_WARP)
+  if (families & LB_TUNE_MP_WARP) {
     for (int ipt : {8, 4, 16}) v.push_back({LB_MERGE_PATH, ipt, 0, 0});
+    for (int units : {4, 8}) v.push_back({LB_MERGE_PATH, 8, 0, 0, units});
+  }
   if (families & LB_TUNE_MP_CTA) {
     for (int ipt : {4, 8}) v.push_back({LB_MERGE_PATH, ipt, 0, 1});
     if (aligned)
@@ -77,6 +80,7 @@ lb_plan_opts_t opts_of(const Candidate& c, int32_t num_cols) {
   o.items_per_thread = c.ipt ? c.ipt : 8;
   o.group_size = c.group;
   o.mp_variant = c.variant;
+  o.units_per_cta = c.units;
   return o;
 }
 
@@ -231,7 +235,9 @@ lb_status_t lb_autotune(const int32_t* tile_offsets, int32_t num_tiles, int32_t 
       r.items_per_thread = c.ipt;
       r.group_size = c.group;
       r.mp_variant = c.variant;
-      if ((c.schedule == prior) && heur < 0 && (c.schedule != LB_MERGE_PATH || (c.ipt == 8 && c.variant == 0)))
+      r.units_per_cta = c.units;
+      if ((c.schedule == prior) && heur < 0 &&
+          (c.schedule != LB_MERGE_PATH || (c.ipt == 8 && c.variant == 0 && c.units == 1)))
         heur = i;
       if (num_tiles == 0) {
         r.status = LB_OK;

@@ -40,7 +40,8 @@ struct MpTable {
   int variant = 0;  // lb_plan_opts_t.mp_variant: 0 warp workers, 1 per-thread search, 2 CTA tiles + bulk copies
   int items_per_tile = 0;
   int grid = 0;          // CTAs launched
-  int workers = 0;       // owners of split-table shares (warps for variant 0, CTAs otherwise)
+  int workers = 0;       // owners of split-table shares (warps for variant 0, CTAs otherwise), per wave;
+                         // for variant 0 workers / 8 work units per wave
   int tiles_per_cta = 0; // tiles per worker
   int64_t entries = 0;
   int64_t items = 0;
@@ -116,7 +117,7 @@ namespace lbh {
 lb_status_t build_mp_table(MpTable& t, const int32_t* rp, int32_t R, int64_t N, int ipt, int variant, int num_sms,
                            int ctas_per_sm, const BatchBases* batch, cudaStream_t s,
                            const int64_t* item_prefix = nullptr, const int64_t* row_prefix = nullptr,
-                           int num_mats = 0, int wave_items = 0);
+                           int num_mats = 0, int wave_items = 0, int units_per_cta = 1);
 lb_status_t launch_mp_spmv(const MpTable& t, const SpmvCall& c, cudaStream_t s);
 // dvals[j] = dy[row(j)] * x[idx[j]] (dvals != null) or tile_of_atom[j] = row(j)
 lb_status_t launch_mp_expand(const MpTable& t, const SpmvCall& c, const float* dy, float* dvals,

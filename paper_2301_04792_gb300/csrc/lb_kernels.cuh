@@ -814,14 +814,15 @@ __device__ __forceinline__ void load_lane_atoms(const int32_t* __restrict__ idx,
 // the running carry; every other row marks the slot of its last atom.  Lane l
 // takes rows l, l + 32, ...; the previous row's end comes from the next-lower
 // lane (a shuffle) instead of a second load.
+// e_pre: rp[i0 + 1 + lane] when lane < nrows (loaded ahead by the caller).
 template <int IPT, bool WRITE_Y>
 __device__ __forceinline__ void warp_row_pass(const int32_t* __restrict__ rp, int i0, int nrows, int j0, int off,
-                                              float carry, WarpScratch<IPT>& sc) {
+                                              float carry, int e_pre, WarpScratch<IPT>& sc) {
   const int lane = threadIdx.x & 31;
   int last_e = -1;  // end of row r - 32 seen by lane 31, carried to lane 0
   for (int rb = 0; rb < nrows; rb += 32) {
     const int r = rb + lane;
-    const int e = r < nrows ? __ldg(rp + i0 + 1 + r) - j0 : 0;
+    const int e = r < nrows ? (rb == 0 ? e_pre : __ldg(rp + i0 + 1 + r)) - j0 : 0;
     int pe = __shfl_up_sync(kFull, e, 1);
     if (lane == 0) pe = last_e;
     last_e = __shfl_sync(kFull, e, 31);
@@ -895,15 +896,18 @@ __global__ void __launch_bounds__(256, IPT <= 8 ? 4 : 2) mp_spmv_warp_kernel(MpA
   // of dx (PERM); the single-matrix forward drops the wave logic
   constexpr bool kMayWave = XB || PERM;
   const int nwaves = kMayWave && a.waves ? a.num_waves : 1;
-  const int nunits = nwaves * a.num_ctas;
-  // Work unit u = the 8 consecutive warp shares (u mod num_ctas) * 8 + warp of
-  // wave u / num_ctas.  One wave: unit blockIdx.x only.  Several waves: units
-  // are taken in order from a counter, so the CTAs work on the earliest open
-  // shares and the data in use spans about one wave however long the batch.
+  const int upw = a.num_workers / WPB;  // work units per wave
+  const int nunits = nwaves * upw;
+  // Work unit u = the 8 consecutive warp shares (u mod upw) * 8 + warp of wave
+  // u / upw.  With more units than CTAs the units are taken in order from a
+  // counter: a CTA that finishes early takes the next open unit, and in a
+  // batch all CTAs work on the earliest open shares, so the data in use spans
+  // about one wave however long the batch.
+  const bool dynamic = nunits > (int)gridDim.x;
   int u = blockIdx.x;
   for (int it = 0; u < nunits; ++it) {
-  const int wave = u / a.num_ctas;
-  const int w = (u - wave * a.num_ctas) * WPB + warp;
+  const int wave = u / upw;
+  const int w = (u - wave * upw) * WPB + warp;
   int64_t ebase = 0;
   int tpc = a.tiles_per_cta;
   int row_end = a.num_tiles;
@@ -939,16 +943,16 @@ __global__ void __launch_bounds__(256, IPT <= 8 ? 4 : 2) mp_spmv_warp_kernel(MpA
     }
   };
 
+  // row ends of the first 32 rows of a tile, one per lane, loaded a tile ahead
+  auto load_ends = [&](int2 t0, int2 t1) {
+    return lane < t1.x - t0.x ? __ldg(a.rp + t0.x + 1 + lane) : 0;
+  };
   float carry = 0.f;
-  int c_cur[IPT], vb_cur[IPT];
-  int2 c1 = c0;
-  if (ntiles > 0) {
-    c1 = spl.get(1);
-    load_atoms(c0, c1, c_cur, vb_cur);
-  }
-  for (int k = 0; k < ntiles; ++k) {
-    const int nrows = c1.x - c0.x, nnz = c1.y - c0.y, j0 = c0.y, off = j0 & 3;
-    // gathers of tile k
+  // gathers of tile k = (t0, t1) whose atoms are in c / vb: x[col] and the
+  // value (read through perm for the transposed tile set); 0 past the tile
+  auto gather_tile = [&](int k, int2 t0, int2 t1, const int (&c)[IPT], const int (&vb)[IPT], float (&xg)[IPT],
+                         float (&vv)[IPT]) {
+    const int nnz = t1.y - t0.y, j0 = t0.y, off = j0 & 3;
     int m0 = 0, m1 = 0;
     int64_t xb0 = 0;
     if constexpr (XB) {
@@ -956,27 +960,24 @@ __global__ void __launch_bounds__(256, IPT <= 8 ? 4 : 2) mp_spmv_warp_kernel(MpA
       m1 = __ldg(sm + k + 1);
       xb0 = __ldg(a.vec_base + m0);
     }
-    float xg[IPT], vv[IPT];
 #pragma unroll
     for (int q = 0; q < IPT; ++q) {
       const int l = s0 + q - off;
       xg[q] = 0.f;
       vv[q] = 0.f;
       if ((unsigned)l < (unsigned)nnz) {
-        xg[q] = at.gather(c_cur[q], atom_xbase<XB>(a, m0, m1, xb0, (int64_t)j0 + l));
-        vv[q] = PERM ? __ldg(at.val + vb_cur[q]) : __int_as_float(vb_cur[q]);
+        xg[q] = at.gather(c[q], atom_xbase<XB>(a, m0, m1, xb0, (int64_t)j0 + l));
+        vv[q] = PERM ? __ldg(at.val + vb[q]) : __int_as_float(vb[q]);
       }
     }
-    // atoms of tile k + 1, in flight while tile k is reduced
-    int2 c2 = c1;
-    if (k + 1 < ntiles) {
-      c2 = spl.get(k + 2);
-      load_atoms(c1, c2, c_cur, vb_cur);
-    }
-    warp_row_pass<IPT, true>(a.rp, c0.x, nrows, j0, off, carry, sc);
-    const float prefix = (nrows > 0 && __ldg(a.rp + c0.x + 1) == j0) ? 0.f : carry;
+  };
+  // tile (t0, t1) with its gathered products: row pass, atom pass, segmented
+  // scan in lane order with the warp's carry in front, coalesced row stores
+  auto reduce_tile = [&](int2 t0, int2 t1, int e_t, const float (&xg)[IPT], const float (&vv)[IPT]) {
+    const int nrows = t1.x - t0.x, j0 = t0.y, off = j0 & 3;
+    warp_row_pass<IPT, true>(a.rp, t0.x, nrows, j0, off, carry, e_t, sc);
+    const float prefix = (nrows > 0 && __shfl_sync(kFull, e_t, 0) == j0) ? 0.f : carry;
     __syncwarp();
-
     const unsigned bits = sc.bits[s0 >> 5] >> (s0 & 31);
     float acc = 0.f, first = 0.f;
     int any = 0, first_row = 0;
@@ -995,7 +996,6 @@ __global__ void __launch_bounds__(256, IPT <= 8 ? 4 : 2) mp_spmv_warp_kernel(MpA
         acc = 0.f;
       }
     }
-    // segmented scan over the lanes, the warp's carry in front of lane 0
     float v = acc;
     int f = any;
 #pragma unroll
@@ -1013,9 +1013,33 @@ __global__ void __launch_bounds__(256, IPT <= 8 ? 4 : 2) mp_spmv_warp_kernel(MpA
     carry = __shfl_sync(kFull, v, 31);
     if (any) sc.y[first_row] = excl + first;
     __syncwarp();
-    for (int r = lane; r < nrows; r += 32) a.out[c0.x + r] = sc.y[r];
+    for (int r = lane; r < nrows; r += 32) a.out[t0.x + r] = sc.y[r];
     if (lane < IPT) sc.bits[lane] = 0u;
     __syncwarp();
+  };
+
+  int c_cur[IPT], vb_cur[IPT];  // atoms of the next tile to gather
+  int2 c1 = c0;
+  int e_cur = 0;
+  if (ntiles > 0) {
+    c1 = spl.get(1);
+    load_atoms(c0, c1, c_cur, vb_cur);
+    e_cur = load_ends(c0, c1);
+  }
+  // per tile: gather it, load the next tile's atoms (in flight while it is
+  // reduced), reduce it
+  for (int k = 0; k < ntiles; ++k) {
+    float xg[IPT], vv[IPT];
+    gather_tile(k, c0, c1, c_cur, vb_cur, xg, vv);
+    int2 c2 = c1;
+    int e_next = 0;
+    if (k + 1 < ntiles) {
+      c2 = spl.get(k + 2);
+      load_atoms(c1, c2, c_cur, vb_cur);
+      e_next = load_ends(c1, c2);
+    }
+    reduce_tile(c0, c1, e_cur, xg, vv);
+    e_cur = e_next;
     c0 = c1;
     c1 = c2;
   }
@@ -1027,7 +1051,7 @@ __global__ void __launch_bounds__(256, IPT <= 8 ? 4 : 2) mp_spmv_warp_kernel(MpA
     s_crow[it & 1][warp] = c0.x < row_end ? c0.x : -1;
     s_cval[it & 1][warp] = carry;
   }
-  if (threadIdx.x == 0) s_unit[it & 1] = nwaves > 1 ? (int)gridDim.x + (int)atomicAdd(a.ticket + 1, 1u) : nunits;
+  if (threadIdx.x == 0) s_unit[it & 1] = dynamic ? (int)gridDim.x + (int)atomicAdd(a.ticket + 1, 1u) : nunits;
   __syncthreads();
   if (warp == 0) {
     const int row = lane < WPB ? s_crow[it & 1][lane] : -5;
@@ -1052,7 +1076,7 @@ __global__ void __launch_bounds__(256, IPT <= 8 ? 4 : 2) mp_spmv_warp_kernel(MpA
   }  // units
   // rows split between CTAs, all waves at once (a wave's rows are never
   // touched by a later wave, and the slots of all waves are in row order)
-  if (cta_ticket(a, &s_last)) last_cta_fixup<256>(a, nwaves * a.num_ctas, s_wv, s_wf, s_incl);
+  if (cta_ticket(a, &s_last)) last_cta_fixup<256>(a, nunits, s_wv, s_wf, s_incl);
 }
 
 // Warp-worker expand: the tile of every atom from the same row marks, then
@@ -1072,12 +1096,15 @@ __global__ void __launch_bounds__(256) mp_expand_warp_kernel(MpArgs a) {
   __syncwarp();
   const int s0 = lane * IPT;
   const int nwaves = a.waves ? a.num_waves : 1;
-  const int nunits = nwaves * a.num_ctas;
-  // work units as in mp_spmv_warp_kernel: several waves take them in order
+  const int upw = a.num_workers / WPB;
+  const int nunits = nwaves * upw;
+  // work units as in mp_spmv_warp_kernel, taken in order when there are more
+  // than CTAs
+  const bool dynamic = nunits > (int)gridDim.x;
   int u = blockIdx.x;
   for (int it = 0; u < nunits; ++it) {
-  const int wave = u / a.num_ctas;
-  const int w = (u - wave * a.num_ctas) * WPB + warp;
+  const int wave = u / upw;
+  const int w = (u - wave * upw) * WPB + warp;
   int64_t ebase = 0;
   int tpc = a.tiles_per_cta;
   if (a.waves) {
@@ -1101,7 +1128,8 @@ __global__ void __launch_bounds__(256) mp_expand_warp_kernel(MpArgs a) {
         c[q] = (unsigned)l < (unsigned)nnz ? ld_stream(a.atoms.idx + j0 + l) : 0;
       }
     }
-    warp_row_pass<IPT, false>(a.rp, c0.x, nrows, j0, off, 0.f, sc);
+    const int e_pre = lane < nrows ? __ldg(a.rp + c0.x + 1 + lane) : 0;
+    warp_row_pass<IPT, false>(a.rp, c0.x, nrows, j0, off, 0.f, e_pre, sc);
     __syncwarp();
     const unsigned bits = (sc.bits[s0 >> 5] >> (s0 & 31)) & (IPT == 32 ? 0xffffffffu : ((1u << IPT) - 1u));
     // first marked slot of each later lane: suffix minimum over the lanes
@@ -1144,7 +1172,7 @@ __global__ void __launch_bounds__(256) mp_expand_warp_kernel(MpArgs a) {
     __syncwarp();
     c0 = c1;
   }
-  if (nwaves > 1) {
+  if (dynamic) {
     if (threadIdx.x == 0) s_unit[it & 1] = (int)gridDim.x + (int)atomicAdd(a.ticket + 1, 1u);
     __syncthreads();
     u = s_unit[it & 1];
@@ -1153,7 +1181,7 @@ __global__ void __launch_bounds__(256) mp_expand_warp_kernel(MpArgs a) {
   }
   }  // units
   // the last CTA to finish resets the unit counter for the next launch
-  if (nwaves > 1 && cta_ticket(a, &s_last) && threadIdx.x == 0) {
+  if (dynamic && cta_ticket(a, &s_last) && threadIdx.x == 0) {
     a.ticket[0] = 0u;
     a.ticket[1] = 0u;
   }

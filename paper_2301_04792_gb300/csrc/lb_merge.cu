@@ -253,7 +253,7 @@ __global__ void split_matrix_kernel(const int2* __restrict__ splits, int64_t ent
 
 lb_status_t build_mp_table(MpTable& t, const int32_t* rp, int32_t R, int64_t N, int ipt, int variant, int num_sms,
                            int ctas_per_sm, const BatchBases* batch, cudaStream_t s, const int64_t* item_prefix,
-                           const int64_t* row_prefix, int num_mats, int wave_items) {
+                           const int64_t* row_prefix, int num_mats, int wave_items, int units_per_cta) {
   t.release();
   if (!kernel_tma(ipt, false, false)) {
     set_error("items_per_thread must be 4, 8 or 16");
@@ -276,7 +276,12 @@ lb_status_t build_mp_table(MpTable& t, const int32_t* rp, int32_t R, int64_t N, 
     if (ctas > (int64_t)num_sms * occ) ctas = (int64_t)num_sms * occ;
     if (ctas < 1) ctas = 1;
     t.grid = (int)ctas;
-    t.workers = t.grid * kWarps;
+    // units_per_cta work units of 8 warp shares per CTA, never fewer than 32
+    // items per warp share on average
+    int64_t units = (int64_t)t.grid * std::max(1, units_per_cta);
+    const int64_t max_units = std::max<int64_t>(t.grid, t.items / (32 * kWarps));
+    if (units > max_units) units = max_units;
+    t.workers = (int)(units * kWarps);
     const int64_t share = (t.items + t.workers - 1) / t.workers;
     int64_t tpc = (share + t.items_per_tile - 1) / t.items_per_tile;
     t.tiles_per_cta = (int)(tpc < 1 ? 1 : tpc);
@@ -297,7 +302,7 @@ lb_status_t build_mp_table(MpTable& t, const int32_t* rp, int32_t R, int64_t N, 
   if (variant == 0 && item_prefix && row_prefix && num_mats > 1) {
     const int64_t min_items =
         wave_items > 0 ? (int64_t)wave_items
-                       : std::max<int64_t>((int64_t)4 << 20, (int64_t)t.workers * t.items_per_tile * 2);
+                       : std::max<int64_t>((int64_t)4 << 20, (int64_t)t.grid * (kBlock / 32) * t.items_per_tile * 2);
     wave_begin.push_back(0);
     wave_rows.push_back(0);
     for (int m = 1; m < num_mats; ++m) {

@@ -85,7 +85,7 @@ class Plan:
 
     def __init__(self, tile_offsets: torch.Tensor, num_atoms: int | None = None, schedule="merge_path",
                  num_cols: int = 0, items_per_thread: int = 0, group_size: int = 0, ctas_per_sm: int = 0,
-                 validate: bool = False, mp_variant: int = 0, stream=None):
+                 validate: bool = False, mp_variant: int = 0, units_per_cta: int = 0, stream=None):
         self._lib = _lib.load()
         _need(tile_offsets, torch.int32, "tile_offsets")
         self.tile_offsets = tile_offsets
@@ -97,7 +97,8 @@ class Plan:
         self.num_atoms = int(num_atoms)
         self.num_cols = int(num_cols)
         opts = PlanOpts(num_cols=int(num_cols), items_per_thread=int(items_per_thread), group_size=int(group_size),
-                        ctas_per_sm=int(ctas_per_sm), validate=int(bool(validate)), mp_variant=int(mp_variant))
+                        ctas_per_sm=int(ctas_per_sm), validate=int(bool(validate)), mp_variant=int(mp_variant),
+                        units_per_cta=int(units_per_cta))
         h = ctypes.c_void_p()
         check(self._lib.lb_plan_ex(ctypes.byref(h), _ptr(tile_offsets), self.num_tiles, self.num_atoms,
                                    int(Schedule.parse(schedule)), ctypes.byref(opts), ctypes.c_void_p(_stream(stream))),
@@ -208,7 +209,8 @@ class Plan:
 def _candidate_name(c) -> str:
     s = Schedule(c.schedule)
     if s == Schedule.MERGE_PATH:
-        return f"merge_path_ipt{c.items_per_thread}_v{c.mp_variant}"
+        u = f"_u{c.units_per_cta}" if c.units_per_cta > 1 else ""
+        return f"merge_path_ipt{c.items_per_thread}_v{c.mp_variant}{u}"
     if s == Schedule.GROUP_MAPPED:
         return f"group_mapped_g{c.group_size}"
     return s.name.lower()
@@ -242,7 +244,7 @@ def autotune(tile_offsets: torch.Tensor, col_idx: torch.Tensor, vals: torch.Tens
         c = res.candidates[i]
         cands.append({"name": _candidate_name(c), "schedule": Schedule(c.schedule).name.lower(),
                       "items_per_thread": c.items_per_thread, "group_size": c.group_size,
-                      "mp_variant": c.mp_variant, "ms": c.ms, "gbps": c.gbps, "reps": c.reps, "status": c.status})
+                      "mp_variant": c.mp_variant, "units_per_cta": c.units_per_cta, "ms": c.ms, "gbps": c.gbps, "reps": c.reps, "status": c.status})
     report = {"candidates": cands, "best": cands[res.best]["name"],
               "heuristic": cands[res.heuristic]["name"] if res.heuristic >= 0 else None,
               "from_cache": bool(res.from_cache), "best_schedule": Schedule(res.best_schedule).name.lower(),
@@ -259,7 +261,7 @@ class BatchPlan:
     """One persistent merge-path plan over a batch of CSR matrices."""
 
     def __init__(self, rows, cols, nnz, rp_cat: torch.Tensor, items_per_thread: int = 0, ctas_per_sm: int = 0,
-                 mp_variant: int = 0, wave_items: int = 0, stream=None):
+                 mp_variant: int = 0, wave_items: int = 0, units_per_cta: int = 0, stream=None):
         self._lib = _lib.load()
         _need(rp_cat, torch.int32, "rp_cat")
         self.rows = np.ascontiguousarray(rows, dtype=np.int32)
@@ -274,7 +276,7 @@ class BatchPlan:
         self.total_cols = int(self.cols.sum())
         self.total_nnz = int(self.nnz.sum())
         opts = PlanOpts(items_per_thread=int(items_per_thread), ctas_per_sm=int(ctas_per_sm),
-                        mp_variant=int(mp_variant), wave_items=int(wave_items))
+                        mp_variant=int(mp_variant), wave_items=int(wave_items), units_per_cta=int(units_per_cta))
         h = ctypes.c_void_p()
         check(self._lib.lb_batch_plan(ctypes.byref(h), self.rows.shape[0], self.rows.ctypes.data_as(ctypes.c_void_p),
                                       self.cols.ctypes.data_as(ctypes.c_void_p),

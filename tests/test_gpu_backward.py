@@ -13,7 +13,8 @@ BWD_SCHEDULES = [("thread_mapped", {}), ("warp_mapped", {}), ("block_mapped", {}
                  ("group_mapped", {"group_size": 8}), ("merge_path", {"items_per_thread": 4}),
                  ("merge_path", {"items_per_thread": 8}), ("merge_path", {"items_per_thread": 16}),
                  ("merge_path", {"items_per_thread": 8, "mp_variant": 1}),
-                 ("merge_path", {"items_per_thread": 8, "mp_variant": 2})]
+                 ("merge_path", {"items_per_thread": 8, "mp_variant": 2}),
+                 ("merge_path", {"items_per_thread": 8, "units_per_cta": 8})]
 
 
 @pytest.fixture(scope="module")

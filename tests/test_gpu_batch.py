@@ -40,14 +40,15 @@ def make_plan(lb, b, **kw):
     return plan, rp_cat, ci, v
 
 
-def check_batch(lb, b, ipts=(8,), variants=(0, 1, 2), wave_items=0):
+def check_batch(lb, b, ipts=(8,), variants=(0, 1, 2), wave_items=0, units=0):
     import torch
     xs, dys = batch_inputs(b)
     y64, yb, dx64, dxb, dv32 = oracle_batch(b, xs, dys)
     xd, dyd = to_dev(np.concatenate(xs), np.concatenate(dys))
     row_of = np.concatenate([oracle.row_of_atom(m.rp) for m in b.mats])
     for ipt, var in [(i, v) for i in ipts for v in variants]:
-        plan, rp_cat, ci, v = make_plan(lb, b, items_per_thread=ipt, mp_variant=var, wave_items=wave_items)
+        plan, rp_cat, ci, v = make_plan(lb, b, items_per_thread=ipt, mp_variant=var, wave_items=wave_items,
+                                        units_per_cta=units)
         ys = [plan.spmv(ci, v, xd) for _ in range(3)]
         assert_within_bound(ys[0].cpu().numpy(), y64, yb, "batch y")
         for y in ys[1:]:
@@ -66,6 +67,7 @@ def check_batch(lb, b, ipts=(8,), variants=(0, 1, 2), wave_items=0):
 def test_small_batch(lbmod):
     b = W.batch(num=40, rmin=50, rmax=5000, mmin=1, mmax=64, seed=3)
     check_batch(lbmod, b, ipts=(4, 8, 16))
+    check_batch(lbmod, b, ipts=(8,), variants=(0,), units=8)  # dynamic units, one wave
 
 
 def test_small_batch_in_waves(lbmod):
@@ -76,6 +78,7 @@ def test_small_batch_in_waves(lbmod):
         assert plan.info()["num_waves"] > 1
     check_batch(lbmod, b, ipts=(4, 8), variants=(0,), wave_items=20_000)
     check_batch(lbmod, b, ipts=(8,), variants=(0,), wave_items=1)
+    check_batch(lbmod, b, ipts=(4,), variants=(0,), wave_items=20_000, units=4)
 
 
 def test_batch_with_degenerate_members(lbmod):

@@ -24,7 +24,9 @@ SCHEDULES = [("thread_mapped", {}), ("warp_mapped", {}), ("block_mapped", {}),
              ("merge_path", {"items_per_thread": 16, "mp_variant": 1}),
              ("merge_path", {"items_per_thread": 4, "mp_variant": 2}),
              ("merge_path", {"items_per_thread": 8, "mp_variant": 2}),
-             ("merge_path", {"items_per_thread": 16, "mp_variant": 2})]
+             ("merge_path", {"items_per_thread": 16, "mp_variant": 2}),
+             ("merge_path", {"items_per_thread": 8, "units_per_cta": 4}),
+             ("merge_path", {"items_per_thread": 4, "units_per_cta": 16})]
 SCHED_IDS = [s + "".join(f"_{k}{v}" for k, v in o.items()) for s, o in SCHEDULES]
 
 
