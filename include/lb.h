@@ -83,7 +83,11 @@ typedef struct lb_plan_opts_t {
                                passes); 1 = CTAs whose threads each search their own diagonal and walk
                                IPT items in merge order (the per-thread form of Sec. 5.2.1); 2 = CTAs
                                with a bulk-copy (TMA) ring and the two-pass split (needs 16-byte aligned
-                               buffers, else 1 is used) */
+                               buffers, else 1 is used); 3 = warps as in 0 on shares of guided sizes (about
+                               half of a warp's remaining part each, down to tiles_per_share tiles) taken in
+                               merge order from a counter, each share's carry resolved by a decoupled
+                               look-back over the preceding shares' published partial sums (no block
+                               barrier, no fix-up pass; bounded waits report LB_ERR_TIMEOUT) */
   int32_t wave_items;       /* batches, warp workers: minimum rows + atoms of a wave (a run of whole
                                matrices shared out over all workers before the next run starts; keeps
                                the run's vectors in L2); 0 = max(4 Mi, 2 x workers x items_per_tile) */
@@ -93,6 +97,8 @@ typedef struct lb_plan_opts_t {
                                and the launch ends with less idle time (each unit ends in a CTA barrier,
                                so more units pay off only where warps' times vary a lot, e.g. R-MAT);
                                0 or 1 = one static unit per CTA */
+  int32_t tiles_per_share;  /* merge-path variant 3: smallest look-back share in warp tiles (default 1) */
+  int32_t reserved[3];
 } lb_plan_opts_t;
 
 /* What a plan resolved to (for tests, the autotuner and reporting). */

@@ -90,6 +90,7 @@ static lb_plan_opts_t defaults(const lb_plan_opts_t* o) {
   if (d.items_per_thread == 0) d.items_per_thread = 8;
   if (d.group_size == 0) d.group_size = 32;
   if (d.units_per_cta == 0) d.units_per_cta = 1;
+  if (d.tiles_per_share == 0) d.tiles_per_share = 1;
   return d;
 }
 
@@ -245,7 +246,7 @@ lb_status_t lb_plan_ex(lb_plan_t* out, const int32_t* tile_offsets, int32_t num_
   // schedule, the atom->tile walk used by dvals and lb_atom_tiles.
   lb_status_t st = build_mp_table(p->mp, tile_offsets, num_tiles, num_atoms, o.items_per_thread, o.mp_variant,
                                   p->num_sms, o.ctas_per_sm, nullptr, s, nullptr, nullptr, 0, 0,
-                                  o.units_per_cta);
+                                  o.units_per_cta, o.tiles_per_share);
   if (st != LB_OK) return fail(st);
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
@@ -387,7 +388,8 @@ lb_status_t lb_prepare_backward(lb_plan_t p, int32_t num_cols, const int32_t* co
     return st;
   }
   st = build_mp_table(p->mp_t, p->cp, num_cols, N, p->opts.items_per_thread, p->opts.mp_variant, p->num_sms,
-                      p->opts.ctas_per_sm, nullptr, s, nullptr, nullptr, 0, 0, p->opts.units_per_cta);
+                      p->opts.ctas_per_sm, nullptr, s, nullptr, nullptr, 0, 0, p->opts.units_per_cta,
+                      p->opts.tiles_per_share);
   if (st != LB_OK) {
     free_transpose(p);
     return st;

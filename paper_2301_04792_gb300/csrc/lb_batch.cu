@@ -111,6 +111,7 @@ lb_status_t lb_batch_plan(lb_plan_t* out, int32_t num_mats, const int32_t* host_
   if (opts) o = *opts;
   if (o.items_per_thread == 0) o.items_per_thread = 8;
   if (o.units_per_cta == 0) o.units_per_cta = 1;
+  if (o.tiles_per_share == 0) o.tiles_per_share = 1;
   if (o.items_per_thread != 4 && o.items_per_thread != 8 && o.items_per_thread != 16) {
     set_error("lb_batch_plan: items_per_thread must be 4, 8 or 16");
     return LB_ERR_UNSUPPORTED;
@@ -160,7 +161,7 @@ lb_status_t lb_batch_plan(lb_plan_t* out, int32_t num_mats, const int32_t* host_
   for (int m = 0; m <= num_mats; ++m) items[m] = rows[m] + nnz[m];
   st = build_mp_table(p->mp, p->rp_global, p->num_tiles, p->num_atoms, o.items_per_thread, o.mp_variant, p->num_sms,
                       o.ctas_per_sm, &p->bb, s, items.data(), rows.data(), num_mats, o.wave_items,
-                      o.units_per_cta);
+                      o.units_per_cta, o.tiles_per_share);
   if (st != LB_OK) return fail(st, "");
   if (cudaStreamSynchronize(s) != cudaSuccess) return fail(LB_ERR_CUDA, "lb_batch_plan: split kernel failed");
   cudaFree(d_rows);
@@ -238,7 +239,7 @@ lb_status_t lb_batch_prepare_backward(lb_plan_t p, const int32_t* col_cat, void*
   for (int m = 0; m <= num; ++m) titems[m] = hc[m] + hn[m];
   st = build_mp_table(p->mp_t, p->cp, C, N, p->opts.items_per_thread, p->opts.mp_variant, p->num_sms,
                       p->opts.ctas_per_sm, nullptr, s, titems.data(), hc.data(), num, p->opts.wave_items,
-                      p->opts.units_per_cta);
+                      p->opts.units_per_cta, p->opts.tiles_per_share);
   if (st != LB_OK) return fail(st, "");
   if (cudaStreamSynchronize(s) != cudaSuccess) return fail(LB_ERR_CUDA, "lb_batch_prepare_backward: sync failed");
   p->has_t = true;

@@ -37,7 +37,8 @@ constexpr int kBlock = 256;
 struct MpTable {
   bool built = false;
   int ipt = 8;
-  int variant = 0;  // lb_plan_opts_t.mp_variant: 0 warp workers, 1 per-thread search, 2 CTA tiles + bulk copies
+  int variant = 0;  // lb_plan_opts_t.mp_variant: 0 warp workers, 1 per-thread search, 2 CTA tiles + bulk copies,
+                    // 3 warp workers on dynamic shares with a look-back fix-up
   int items_per_tile = 0;
   int grid = 0;          // CTAs launched
   int workers = 0;       // owners of split-table shares (warps for variant 0, CTAs otherwise), per wave;
@@ -53,7 +54,12 @@ struct MpTable {
   void* d_waves = nullptr;    // lbk::WaveDesc[num_waves] when num_waves > 1
   float* carry_val = nullptr; // [num_waves x grid]
   int32_t* carry_row = nullptr;
-  unsigned* ticket = nullptr; // [2]: fix-up ticket, work-unit counter
+  unsigned* ticket = nullptr; // [4]: fix-up ticket, work counter, look-back epoch, spare
+  // variant 3 (guided look-back shares, num_workers of them): first split
+  // entry of every share [S + 1], its first two splits [S], published records [S]
+  int64_t* share_ent = nullptr;
+  int4* share_head = nullptr;
+  unsigned long long* records = nullptr;
   void release();
 };
 
@@ -117,7 +123,8 @@ namespace lbh {
 lb_status_t build_mp_table(MpTable& t, const int32_t* rp, int32_t R, int64_t N, int ipt, int variant, int num_sms,
                            int ctas_per_sm, const BatchBases* batch, cudaStream_t s,
                            const int64_t* item_prefix = nullptr, const int64_t* row_prefix = nullptr,
-                           int num_mats = 0, int wave_items = 0, int units_per_cta = 1);
+                           int num_mats = 0, int wave_items = 0, int units_per_cta = 1,
+                           int tiles_per_share = 1);
 lb_status_t launch_mp_spmv(const MpTable& t, const SpmvCall& c, cudaStream_t s);
 // dvals[j] = dy[row(j)] * x[idx[j]] (dvals != null) or tile_of_atom[j] = row(j)
 lb_status_t launch_mp_expand(const MpTable& t, const SpmvCall& c, const float* dy, float* dvals,
@@ -137,6 +144,8 @@ int device_sms(int device);
 int64_t mp_diagonal(int64_t items, int grid, int tiles_per_cta, int items_per_tile, int64_t e);
 void mp_geometry(int64_t items, int grid_cap, int items_per_tile, int block, int* grid, int* tiles_per_cta);
 int occupancy_mp(int ipt, int variant);
+// variants whose workers are warps (the warp expand kernel serves their tables)
+inline bool warp_workers(int variant) { return variant == 0 || variant == 3; }
 lb_status_t check_columns(const int32_t* ci, int64_t n, int32_t C, cudaStream_t s);
 
 }  // namespace lbh

@@ -25,6 +25,7 @@ constexpr int kDevErrColumn = 1;   // device error bit: column index out of rang
 constexpr int kDevErrTimeout = 2;  // device error bit: a bounded wait gave up
 constexpr int kStages = 3;         // shared-memory ring depth of the merge-path pipeline
 constexpr long long kSpinLimit = 1LL << 26;
+constexpr long long kLookbackSpins = 1LL << 22;  // with 64 ns sleeps: a few tenths of a second
 
 // ------------------------------------------------------------- load helpers --
 
@@ -199,7 +200,13 @@ struct MpArgs {
   int num_waves;
   float* carry_val;         // [num_waves x num_ctas], one slot per work unit
   int32_t* carry_row;       // [num_waves x num_ctas]
-  unsigned* ticket;         // [0] fix-up ticket, [1] next work unit; both zero between launches
+  unsigned* ticket;         // [0] fix-up ticket, [1] next work unit (zero between launches), [2] launch
+                            // epoch of the look-back flags (never 0)
+  // look-back kernel (guided shares): first split entry of every share [S + 1],
+  // its first two split entries, and the published records [S]
+  const int64_t* share_ent;
+  const int4* share_head;
+  unsigned long long* records;
   int* status;
   // expand kernels
   const float* dy;          // dvals: upstream gradient per tile
@@ -859,105 +866,72 @@ struct WarpSplits {
   }
 };
 
-// Merge-path SpMV (Sec. 5.2.1) with warps as the workers.  The plan's split
-// table gives every warp an equal share of rows + atoms, cut into warp tiles
-// of 32 * IPT - 4 merge items, each split found by the search along its
-// diagonal.  A warp walks its share tile by tile with no block-wide barrier:
-// per tile its lanes gather the dense vector for the tile's atoms (loaded as
-// 16-byte vectors one tile ahead), split the tile's rows evenly (row pass:
-// empty rows 0, marks at each row's last atom) and its atoms evenly (IPT
-// consecutive atoms per lane, closing a row at each mark); a warp-shuffle
-// segmented scan in lane order, with the warp's running carry in front,
-// resolves rows that cross lanes.  Rows split between warps are fixed up by
-// the last CTA to finish.
+// One warp's walk over one merge-path share (Sec. 5.2.1): the share's
+// split-table entries start at `wbase` (tpc + 1 of them, the last one its
+// end).  Tile by tile (32 * IPT - 4 merge items) the lanes gather the dense
+// vector for the tile's atoms (atoms loaded as 16-byte vectors one tile
+// ahead), split the tile's rows evenly (row pass: empty rows 0, marks at each
+// row's last atom) and its atoms evenly (IPT consecutive atoms per lane,
+// closing a row at each mark); a warp-shuffle segmented scan in lane order,
+// with the running carry in front, resolves rows that cross lanes, and the
+// tile's finished rows are stored together.  The row open at the share's
+// start gets only this share's part; walk() returns the split at the share's
+// end, with the partial sum of the row left open there in `carry`.
 // VEC: idx and val (or perm) are 16-byte aligned (vector loads); otherwise
 // every atom is loaded on its own.
 template <int IPT, bool XB, bool PERM, bool VEC>
-__global__ void __launch_bounds__(256, IPT <= 8 ? 4 : 2) mp_spmv_warp_kernel(MpArgs a) {
+struct WarpWalker {
   static_assert(IPT % 4 == 0 && 32 % IPT == 0, "IPT must be 4, 8 or 16");
-  constexpr int WPB = 8;
-  __shared__ WarpScratch<IPT> sc_all[WPB];
-  __shared__ float s_wv[WPB];
-  __shared__ int s_wf[WPB];
-  __shared__ float s_incl[256];
-  __shared__ int s_last;
-  __shared__ int s_crow[2][WPB];  // by unit parity: a warp may write its next unit's carry while
-  __shared__ float s_cval[2][WPB];  // warp 0 still reads this unit's
-  __shared__ int s_unit[2];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  WarpScratch<IPT>& sc = sc_all[warp];
-  const AtomView& at = a.atoms;
-  const int32_t* vsrc = PERM ? at.perm : reinterpret_cast<const int32_t*>(at.val);
+  const MpArgs& a;
+  WarpScratch<IPT>& sc;
+  const int lane, s0;
+  const int32_t* vsrc;
 
-  if (lane < IPT) sc.bits[lane] = 0u;
-  __syncwarp();
-  const int s0 = lane * IPT;
-  // tables in waves come from batches: the forward (XB) or the transposed one
-  // of dx (PERM); the single-matrix forward drops the wave logic
-  constexpr bool kMayWave = XB || PERM;
-  const int nwaves = kMayWave && a.waves ? a.num_waves : 1;
-  const int upw = a.num_workers / WPB;  // work units per wave
-  const int nunits = nwaves * upw;
-  // Work unit u = the 8 consecutive warp shares (u mod upw) * 8 + warp of wave
-  // u / upw.  With more units than CTAs the units are taken in order from a
-  // counter: a CTA that finishes early takes the next open unit, and in a
-  // batch all CTAs work on the earliest open shares, so the data in use spans
-  // about one wave however long the batch.
-  const bool dynamic = nunits > (int)gridDim.x;
-  int u = blockIdx.x;
-  for (int it = 0; u < nunits; ++it) {
-  const int wave = u / upw;
-  const int w = (u - wave * upw) * WPB + warp;
-  int64_t ebase = 0;
-  int tpc = a.tiles_per_cta;
-  int row_end = a.num_tiles;
-  if (kMayWave && a.waves) {
-    ebase = a.waves[wave].entry_base;
-    tpc = a.waves[wave].tpc;
-    row_end = a.waves[wave].row_end;
-  }
-  const size_t wbase = (size_t)ebase + (size_t)w * (tpc + 1);
-  WarpSplits spl{a.splits + wbase, tpc + 1};
-  const int32_t* sm = XB ? a.split_m + wbase : nullptr;
-  int2 c0 = spl.get(0);
-  int ntiles;
-  {
-    const int2 e1 = __ldg(a.splits + wbase + tpc);
-    const int64_t share = (int64_t)(e1.x - c0.x) + (e1.y - c0.y);
-    ntiles = (int)((share + a.items_per_tile - 1) / a.items_per_tile);
+  __device__ __forceinline__ WarpWalker(const MpArgs& args, WarpScratch<IPT>& scratch)
+      : a(args), sc(scratch), lane(threadIdx.x & 31), s0((threadIdx.x & 31) * IPT),
+        vsrc(PERM ? args.atoms.perm : reinterpret_cast<const int32_t*>(args.atoms.val)) {
+    if (lane < IPT) sc.bits[lane] = 0u;
+    __syncwarp();
   }
 
-  // this lane's atom indices and values (or perm) of a tile
-  auto load_atoms = [&](int2 t0, int2 t1, int* c, int* vb) {
+  // tiles of a share whose split entries run from t0 to e1
+  __device__ __forceinline__ int num_tiles(int2 t0, int2 e1) const {
+    const int64_t share = (int64_t)(e1.x - t0.x) + (e1.y - t0.y);
+    return (int)((share + a.items_per_tile - 1) / a.items_per_tile);
+  }
+
+  // this lane's atom indices and values (or perm) of tile (t0, t1)
+  __device__ __forceinline__ void load_atoms(int2 t0, int2 t1, int (&c)[IPT], int (&vb)[IPT]) const {
     const int j0 = t0.y, off = j0 & 3, nnz = t1.y - t0.y;
     if constexpr (VEC) {
-      load_lane_atoms<IPT>(at.idx, vsrc, (int64_t)(j0 - off), s0, t1.y, a.num_atoms, c, vb);
+      load_lane_atoms<IPT>(a.atoms.idx, vsrc, (int64_t)(j0 - off), s0, t1.y, a.num_atoms, c, vb);
     } else {
 #pragma unroll
       for (int q = 0; q < IPT; ++q) {
         const int l = s0 + q - off;
         const bool in = (unsigned)l < (unsigned)nnz;
-        c[q] = in ? ld_stream(at.idx + j0 + l) : 0;
+        c[q] = in ? ld_stream(a.atoms.idx + j0 + l) : 0;
         vb[q] = in ? ld_stream(vsrc + j0 + l) : 0;
       }
     }
-  };
+  }
 
-  // row ends of the first 32 rows of a tile, one per lane, loaded a tile ahead
-  auto load_ends = [&](int2 t0, int2 t1) {
+  // row ends of the first 32 rows of tile (t0, t1), one per lane
+  __device__ __forceinline__ int load_ends(int2 t0, int2 t1) const {
     return lane < t1.x - t0.x ? __ldg(a.rp + t0.x + 1 + lane) : 0;
-  };
-  float carry = 0.f;
-  // gathers of tile k = (t0, t1) whose atoms are in c / vb: x[col] and the
-  // value (read through perm for the transposed tile set); 0 past the tile
-  auto gather_tile = [&](int k, int2 t0, int2 t1, const int (&c)[IPT], const int (&vb)[IPT], float (&xg)[IPT],
-                         float (&vv)[IPT]) {
+  }
+
+  // gathers of tile (t0, t1) whose atoms are in c / vb: x[col] and the value
+  // (read through perm for the transposed tile set); 0 past the tile.  sm: the
+  // matrix of the tile's first and last split (batches)
+  __device__ __forceinline__ void gather_tile(const int32_t* sm, int2 t0, int2 t1, const int (&c)[IPT],
+                                              const int (&vb)[IPT], float (&xg)[IPT], float (&vv)[IPT]) const {
     const int nnz = t1.y - t0.y, j0 = t0.y, off = j0 & 3;
     int m0 = 0, m1 = 0;
     int64_t xb0 = 0;
     if constexpr (XB) {
-      m0 = __ldg(sm + k);
-      m1 = __ldg(sm + k + 1);
+      m0 = __ldg(sm);
+      m1 = __ldg(sm + 1);
       xb0 = __ldg(a.vec_base + m0);
     }
 #pragma unroll
@@ -966,14 +940,17 @@ __global__ void __launch_bounds__(256, IPT <= 8 ? 4 : 2) mp_spmv_warp_kernel(MpA
       xg[q] = 0.f;
       vv[q] = 0.f;
       if ((unsigned)l < (unsigned)nnz) {
-        xg[q] = at.gather(c[q], atom_xbase<XB>(a, m0, m1, xb0, (int64_t)j0 + l));
-        vv[q] = PERM ? __ldg(at.val + vb[q]) : __int_as_float(vb[q]);
+        xg[q] = a.atoms.gather(c[q], atom_xbase<XB>(a, m0, m1, xb0, (int64_t)j0 + l));
+        vv[q] = PERM ? __ldg(a.atoms.val + vb[q]) : __int_as_float(vb[q]);
       }
     }
-  };
+  }
+
   // tile (t0, t1) with its gathered products: row pass, atom pass, segmented
-  // scan in lane order with the warp's carry in front, coalesced row stores
-  auto reduce_tile = [&](int2 t0, int2 t1, int e_t, const float (&xg)[IPT], const float (&vv)[IPT]) {
+  // scan in lane order with the running carry in front, coalesced row stores;
+  // e_t = load_ends(t0, t1)
+  __device__ __forceinline__ void reduce_tile(int2 t0, int2 t1, int e_t, const float (&xg)[IPT],
+                                              const float (&vv)[IPT], float& carry) {
     const int nrows = t1.x - t0.x, j0 = t0.y, off = j0 & 3;
     warp_row_pass<IPT, true>(a.rp, t0.x, nrows, j0, off, carry, e_t, sc);
     const float prefix = (nrows > 0 && __shfl_sync(kFull, e_t, 0) == j0) ? 0.f : carry;
@@ -1016,67 +993,295 @@ __global__ void __launch_bounds__(256, IPT <= 8 ? 4 : 2) mp_spmv_warp_kernel(MpA
     for (int r = lane; r < nrows; r += 32) a.out[t0.x + r] = sc.y[r];
     if (lane < IPT) sc.bits[lane] = 0u;
     __syncwarp();
-  };
+  }
 
-  int c_cur[IPT], vb_cur[IPT];  // atoms of the next tile to gather
-  int2 c1 = c0;
-  int e_cur = 0;
-  if (ntiles > 0) {
-    c1 = spl.get(1);
-    load_atoms(c0, c1, c_cur, vb_cur);
-    e_cur = load_ends(c0, c1);
-  }
-  // per tile: gather it, load the next tile's atoms (in flight while it is
-  // reduced), reduce it
-  for (int k = 0; k < ntiles; ++k) {
-    float xg[IPT], vv[IPT];
-    gather_tile(k, c0, c1, c_cur, vb_cur, xg, vv);
-    int2 c2 = c1;
-    int e_next = 0;
-    if (k + 1 < ntiles) {
-      c2 = spl.get(k + 2);
-      load_atoms(c1, c2, c_cur, vb_cur);
-      e_next = load_ends(c1, c2);
+  // the share whose split entries start at wbase (tpc + 1 of them): per tile,
+  // gather it, load the next tile's atoms (in flight while it is reduced),
+  // reduce it
+  __device__ __forceinline__ int2 walk(size_t wbase, int tpc, float& carry) {
+    WarpSplits spl{a.splits + wbase, tpc + 1};
+    const int32_t* sm = XB ? a.split_m + wbase : nullptr;
+    int2 c0 = spl.get(0);
+    const int ntiles = num_tiles(c0, __ldg(a.splits + wbase + tpc));
+    carry = 0.f;
+    int c_cur[IPT], vb_cur[IPT];  // atoms of the next tile to gather
+    int2 c1 = c0;
+    int e_cur = 0;
+    if (ntiles > 0) {
+      c1 = spl.get(1);
+      load_atoms(c0, c1, c_cur, vb_cur);
+      e_cur = load_ends(c0, c1);
     }
-    reduce_tile(c0, c1, e_cur, xg, vv);
-    e_cur = e_next;
-    c0 = c1;
-    c1 = c2;
+    for (int k = 0; k < ntiles; ++k) {
+      float xg[IPT], vv[IPT];
+      gather_tile(sm + k, c0, c1, c_cur, vb_cur, xg, vv);
+      int2 c2 = c1;
+      int e_next = 0;
+      if (k + 1 < ntiles) {
+        c2 = spl.get(k + 2);
+        load_atoms(c1, c2, c_cur, vb_cur);
+        e_next = load_ends(c1, c2);
+      }
+      reduce_tile(c0, c1, e_cur, xg, vv, carry);
+      e_cur = e_next;
+      c0 = c1;
+      c1 = c2;
+    }
+    return c0;
   }
-  // Carries between the CTA's own warps (consecutive workers) are settled here,
-  // by every CTA at its end: a segmented scan over the 8 warps' carries keyed
-  // by row; a run that a later warp of this CTA closed is added to its row,
-  // the run left open by the last warp becomes the CTA's carry-out.
-  if (lane == 0) {
-    s_crow[it & 1][warp] = c0.x < row_end ? c0.x : -1;
-    s_cval[it & 1][warp] = carry;
-  }
-  if (threadIdx.x == 0) s_unit[it & 1] = dynamic ? (int)gridDim.x + (int)atomicAdd(a.ticket + 1, 1u) : nunits;
-  __syncthreads();
-  if (warp == 0) {
-    const int row = lane < WPB ? s_crow[it & 1][lane] : -5;
-    float v = lane < WPB ? s_cval[it & 1][lane] : 0.f;
+};
+
+// Merge-path SpMV with warps as the workers and the fix-up of Sec. 5.2.1
+// done inside the launch.  The plan's split table gives every warp worker an
+// equal share of rows + atoms; a WORK UNIT is the 8 consecutive shares of one
+// CTA.  After a unit, the CTA settles the rows split between its own warps (a
+// segmented scan over the 8 warps' carries keyed by row) and leaves one
+// carry; the last CTA to finish combines those in order.
+template <int IPT, bool XB, bool PERM, bool VEC>
+__global__ void __launch_bounds__(256, IPT <= 8 ? 4 : 2) mp_spmv_warp_kernel(MpArgs a) {
+  constexpr int WPB = 8;
+  __shared__ WarpScratch<IPT> sc_all[WPB];
+  __shared__ float s_wv[WPB];
+  __shared__ int s_wf[WPB];
+  __shared__ float s_incl[256];
+  __shared__ int s_last;
+  __shared__ int s_crow[2][WPB];  // by unit parity: a warp may write its next unit's carry while
+  __shared__ float s_cval[2][WPB];  // warp 0 still reads this unit's
+  __shared__ int s_unit[2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  WarpWalker<IPT, XB, PERM, VEC> walker(a, sc_all[warp]);
+  // tables in waves come from batches: the forward (XB) or the transposed one
+  // of dx (PERM); the single-matrix forward drops the wave logic
+  constexpr bool kMayWave = XB || PERM;
+  const int nwaves = kMayWave && a.waves ? a.num_waves : 1;
+  const int upw = a.num_workers / WPB;  // work units per wave
+  const int nunits = nwaves * upw;
+  // Work unit u = the 8 consecutive warp shares (u mod upw) * 8 + warp of wave
+  // u / upw.  With more units than CTAs the units are taken in order from a
+  // counter: a CTA that finishes early takes the next open unit, and in a
+  // batch all CTAs work on the earliest open shares, so the data in use spans
+  // about one wave however long the batch.
+  const bool dynamic = nunits > (int)gridDim.x;
+  int u = blockIdx.x;
+  for (int it = 0; u < nunits; ++it) {
+    const int wave = u / upw;
+    const int w = (u - wave * upw) * WPB + warp;
+    int64_t ebase = 0;
+    int tpc = a.tiles_per_cta;
+    int row_end = a.num_tiles;
+    if (kMayWave && a.waves) {
+      ebase = a.waves[wave].entry_base;
+      tpc = a.waves[wave].tpc;
+      row_end = a.waves[wave].row_end;
+    }
+    float carry;
+    const int2 c_end = walker.walk((size_t)ebase + (size_t)w * (tpc + 1), tpc, carry);
+    if (lane == 0) {
+      s_crow[it & 1][warp] = c_end.x < row_end ? c_end.x : -1;
+      s_cval[it & 1][warp] = carry;
+    }
+    if (threadIdx.x == 0) s_unit[it & 1] = dynamic ? (int)gridDim.x + (int)atomicAdd(a.ticket + 1, 1u) : nunits;
+    __syncthreads();
+    // a run that a later warp of this CTA closed is added to its row, the run
+    // left open by the last warp becomes the unit's carry-out
+    if (warp == 0) {
+      const int row = lane < WPB ? s_crow[it & 1][lane] : -5;
+      float v = lane < WPB ? s_cval[it & 1][lane] : 0.f;
 #pragma unroll
-    for (int o = 1; o < WPB; o <<= 1) {
-      const float vo = __shfl_up_sync(kFull, v, o, WPB);
-      const int ro = __shfl_up_sync(kFull, row, o, WPB);
-      if ((lane & (WPB - 1)) >= o && ro == row) v = vo + v;
+      for (int o = 1; o < WPB; o <<= 1) {
+        const float vo = __shfl_up_sync(kFull, v, o, WPB);
+        const int ro = __shfl_up_sync(kFull, row, o, WPB);
+        if ((lane & (WPB - 1)) >= o && ro == row) v = vo + v;
+      }
+      const int nrow = __shfl_down_sync(kFull, row, 1, WPB);
+      if (lane < WPB - 1 && row >= 0 && nrow != row) {
+        float* py = a.out + row;
+        __stcg(py, __ldcg(py) + v);
+      }
+      if (lane == WPB - 1) {
+        a.carry_row[u] = row;
+        a.carry_val[u] = v;
+      }
     }
-    const int nrow = __shfl_down_sync(kFull, row, 1, WPB);
-    if (lane < WPB - 1 && row >= 0 && nrow != row) {
-      float* py = a.out + row;
-      __stcg(py, __ldcg(py) + v);
-    }
-    if (lane == WPB - 1) {
-      a.carry_row[u] = row;
-      a.carry_val[u] = v;
-    }
+    u = s_unit[it & 1];
   }
-  u = s_unit[it & 1];
-  }  // units
-  // rows split between CTAs, all waves at once (a wave's rows are never
+  // rows split between units, all waves at once (a wave's rows are never
   // touched by a later wave, and the slots of all waves are in row order)
   if (cta_ticket(a, &s_last)) last_cta_fixup<256>(a, nunits, s_wv, s_wf, s_incl);
+}
+
+// Look-back record of share p: (flag << 32) | float bits of its partial sum,
+// flag = (epoch << 1) | FINAL; one 64-bit store publishes both halves.
+__device__ __forceinline__ void publish_record(unsigned long long* rec, unsigned epoch, bool final_, float v) {
+  const unsigned long long w =
+      ((unsigned long long)((epoch << 1) | (final_ ? 1u : 0u)) << 32) | (unsigned long long)__float_as_uint(v);
+  *reinterpret_cast<volatile unsigned long long*>(rec) = w;
+}
+
+// Sum of the partial sums that shares before `s` hold of the row open at s's
+// start: lane l reads record s - 1 - l (32 shares per window); the nearest
+// FINAL record (or share 0) ends the run.  Waits, bounded, until every record
+// up to that one carries this launch's epoch; adds the run with a fixed
+// butterfly per window and the windows in order.  Returns false if a wait
+// gave up.
+__device__ __forceinline__ bool look_back(const unsigned long long* records, int s, unsigned epoch, float& total) {
+  const int lane = threadIdx.x & 31;
+  total = 0.f;
+  for (int base = s - 1; base >= 0; base -= 32) {
+    const int p = base - lane;
+    unsigned long long w = 0;
+    bool ready = p < 0;
+    unsigned term = 0;
+    int j = 31;
+    for (long long spin = 0;; ++spin) {
+      if (!ready) {
+        w = *reinterpret_cast<volatile const unsigned long long*>(records + p);
+        ready = (unsigned)(w >> 33) == epoch;
+      }
+      term = __ballot_sync(kFull, p < 0 || (ready && (((w >> 32) & 1ull) || p == 0)));
+      j = term ? __ffs(term) - 1 : 31;
+      const unsigned need = (2u << j) - 1u;  // lanes 0..j
+      if ((__ballot_sync(kFull, ready) & need) == need) break;
+      if (spin > kLookbackSpins) return false;
+      __nanosleep(64);
+    }
+    float v = (lane <= j && p >= 0) ? __uint_as_float((unsigned)w) : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    total += v;
+    if (term) break;
+  }
+  return true;
+}
+
+// Merge-path SpMV with warps as the workers on dynamically taken shares and
+// the carries resolved by a decoupled look-back (no block barrier, no fix-up
+// pass).  The plan cuts the rows + atoms into num_workers shares of whole warp
+// tiles in merge order, large first and down to tiles_per_share tiles at the
+// end (guided sizes: each share about half the remaining work of one warp),
+// so that the warps finish together.  A warp takes its next share from a
+// counter two tiles before the end of the current one, loads that share's
+// first tile while it reduces its last one, and walks tile after tile with
+// the WarpWalker.  At a share's end it publishes the partial sum of the row
+// left open there, FINAL if the share holds a row end (the open row then
+// started inside it), PARTIAL if the share lies inside one row.  A share that
+// closes a row adds, one share later, the partial sums its predecessors hold
+// of its first row (look_back) to that row.  Every sum has a fixed order, so
+// results do not depend on timing; every share is taken by a running warp and
+// no share waits on a later one, so the waits end (and are bounded all the
+// same: a wait that gives up sets the timeout bit of the status word).
+// Records carry the launch's epoch (ticket[2]), which the last CTA to finish
+// advances, so they need no reset between launches.
+template <int IPT, bool XB, bool PERM, bool VEC>
+__global__ void __launch_bounds__(256, IPT <= 8 ? 4 : 2) mp_spmv_lookback_kernel(MpArgs a) {
+  constexpr int WPB = 8;
+  __shared__ WarpScratch<IPT> sc_all[WPB];
+  __shared__ int s_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  WarpWalker<IPT, XB, PERM, VEC> wk(a, sc_all[warp]);
+  const unsigned epoch = *reinterpret_cast<volatile unsigned*>(a.ticket + 2);
+  const int S = a.num_workers;
+  bool ok = true;
+
+  int s = 0;
+  if (lane == 0) s = (int)atomicAdd(a.ticket + 1, 1u);
+  s = __shfl_sync(kFull, s, 0);
+  // state of share s (split entries < 2^31: the plan checks)
+  int base = 0;
+  int ntiles = 0;
+  int2 c_start = make_int2(0, 0), c0 = c_start, c1 = c_start;
+  int c_cur[IPT], vb_cur[IPT];
+  int e_cur = 0;
+  if (s < S) {
+    base = (int)__ldg(a.share_ent + s);
+    ntiles = (int)__ldg(a.share_ent + s + 1) - base - 1;
+    const int4 h = __ldg(a.share_head + s);
+    c_start = c0 = make_int2(h.x, h.y);
+    c1 = make_int2(h.z, h.w);
+    wk.load_atoms(c0, c1, c_cur, vb_cur);
+    e_cur = wk.load_ends(c0, c1);
+  }
+  WarpSplits spl{a.splits + base, ntiles + 1};
+  float carry = 0.f;
+  int k = 0;
+  int next = S;          // lane 0: the share after s
+  bool taken = false;
+  int pend_s = -1, pend_row = 0;  // share whose first row still needs its predecessors' sums
+  while (s < S) {
+    if (!taken && k + 2 >= ntiles) {
+      if (lane == 0) next = (int)atomicAdd(a.ticket + 1, 1u);
+      taken = true;
+    }
+    float xg[IPT], vv[IPT];
+    wk.gather_tile(XB ? a.split_m + (base + k) : nullptr, c0, c1, c_cur, vb_cur, xg, vv);
+    const bool last = k + 1 == ntiles;
+    int2 c2 = c1;
+    int e_next = 0;
+    int sn = S;
+    if (!last) {
+      c2 = spl.get(k + 2);
+      wk.load_atoms(c1, c2, c_cur, vb_cur);
+      e_next = wk.load_ends(c1, c2);
+    } else {
+      sn = __shfl_sync(kFull, next, 0);
+      if (sn < S) {
+        const int4 hn = __ldg(a.share_head + sn);
+        wk.load_atoms(make_int2(hn.x, hn.y), make_int2(hn.z, hn.w), c_cur, vb_cur);
+        e_next = wk.load_ends(make_int2(hn.x, hn.y), make_int2(hn.z, hn.w));
+      }
+    }
+    wk.reduce_tile(c0, c1, e_cur, xg, vv, carry);
+    e_cur = e_next;
+    if (!last) {
+      c0 = c1;
+      c1 = c2;
+      ++k;
+      continue;
+    }
+    // share s is done; c1 is its end
+    const bool has_end = c1.x > c_start.x;
+    if (lane == 0 && s + 1 < S) publish_record(a.records + s, epoch, has_end, carry);
+    if (pend_s >= 0) {
+      float total;
+      ok = look_back(a.records, pend_s, epoch, total) && ok;
+      if (lane == 0) {
+        float* py = a.out + pend_row;
+        __stcg(py, __ldcg(py) + total);
+      }
+    }
+    pend_s = (has_end && s > 0) ? s : -1;
+    pend_row = c_start.x;
+    // on to share sn, its first tile already loading (its head and entry
+    // base are read again: cached since the loads above)
+    s = sn;
+    if (s < S) {
+      base = (int)__ldg(a.share_ent + s);
+      ntiles = (int)__ldg(a.share_ent + s + 1) - base - 1;
+      const int4 hn = __ldg(a.share_head + s);
+      c_start = c0 = make_int2(hn.x, hn.y);
+      c1 = make_int2(hn.z, hn.w);
+    }
+    spl = WarpSplits{a.splits + base, ntiles + 1};
+    carry = 0.f;
+    k = 0;
+    taken = false;
+  }
+  if (pend_s >= 0) {
+    float total;
+    ok = look_back(a.records, pend_s, epoch, total) && ok;
+    if (lane == 0) {
+      float* py = a.out + pend_row;
+      __stcg(py, __ldcg(py) + total);
+    }
+  }
+  if (!ok && lane == 0 && a.status) atomicOr(a.status, kDevErrTimeout);
+  // the last CTA to finish resets the share counter and advances the epoch
+  if (cta_ticket(a, &s_last) && threadIdx.x == 0) {
+    const unsigned e1 = (epoch + 1u) & 0x7fffffffu;
+    a.ticket[1] = 0u;
+    a.ticket[2] = e1 ? e1 : 1u;
+    a.ticket[0] = 0u;
+  }
 }
 
 // Warp-worker expand: the tile of every atom from the same row marks, then
@@ -1095,92 +1300,113 @@ __global__ void __launch_bounds__(256) mp_expand_warp_kernel(MpArgs a) {
   if (lane < IPT) sc.bits[lane] = 0u;
   __syncwarp();
   const int s0 = lane * IPT;
-  const int nwaves = a.waves ? a.num_waves : 1;
-  const int upw = a.num_workers / WPB;
-  const int nunits = nwaves * upw;
-  // work units as in mp_spmv_warp_kernel, taken in order when there are more
-  // than CTAs
-  const bool dynamic = nunits > (int)gridDim.x;
-  int u = blockIdx.x;
-  for (int it = 0; u < nunits; ++it) {
-  const int wave = u / upw;
-  const int w = (u - wave * upw) * WPB + warp;
-  int64_t ebase = 0;
-  int tpc = a.tiles_per_cta;
-  if (a.waves) {
-    ebase = a.waves[wave].entry_base;
-    tpc = a.waves[wave].tpc;
-  }
-  const int2* sp = a.splits + (size_t)ebase + (size_t)w * (tpc + 1);
-  const int32_t* sm = XB ? a.split_m + (size_t)ebase + (size_t)w * (tpc + 1) : nullptr;
-  int2 c0 = __ldg(sp);
-  const int2 e1 = __ldg(sp + tpc);
-  const int64_t share = (int64_t)(e1.x - c0.x) + (e1.y - c0.y);
-  const int ntiles = (int)((share + a.items_per_tile - 1) / a.items_per_tile);
-  for (int k = 0; k < ntiles; ++k) {
-    const int2 c1 = __ldg(sp + k + 1);
-    const int nrows = c1.x - c0.x, nnz = c1.y - c0.y, j0 = c0.y, off = j0 & 3;
-    int c[IPT];
-    if constexpr (DVALS) {
+  // the ntiles tiles of one share, split entries sp[0..ntiles], matrices sm
+  auto expand_share = [&](const int2* sp, const int32_t* sm, int ntiles) {
+    int2 c0 = __ldg(sp);
+    for (int k = 0; k < ntiles; ++k) {
+      const int2 c1 = __ldg(sp + k + 1);
+      const int nrows = c1.x - c0.x, nnz = c1.y - c0.y, j0 = c0.y, off = j0 & 3;
+      int c[IPT];
+      if constexpr (DVALS) {
+#pragma unroll
+        for (int q = 0; q < IPT; ++q) {
+          const int l = s0 + q - off;
+          c[q] = (unsigned)l < (unsigned)nnz ? ld_stream(a.atoms.idx + j0 + l) : 0;
+        }
+      }
+      const int e_pre = lane < nrows ? __ldg(a.rp + c0.x + 1 + lane) : 0;
+      warp_row_pass<IPT, false>(a.rp, c0.x, nrows, j0, off, 0.f, e_pre, sc);
+      __syncwarp();
+      const unsigned bits = (sc.bits[s0 >> 5] >> (s0 & 31)) & (IPT == 32 ? 0xffffffffu : ((1u << IPT) - 1u));
+      // first marked slot of each later lane: suffix minimum over the lanes
+      int fm = bits ? s0 + __ffs(bits) - 1 : INT_MAX;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int n = __shfl_down_sync(kFull, fm, o);
+        if (lane + o < 32) fm = min(fm, n);
+      }
+      int nxt = __shfl_down_sync(kFull, fm, 1);
+      if (lane == 31) nxt = INT_MAX;
+      int rows_q[IPT];
+#pragma unroll
+      for (int q = IPT - 1; q >= 0; --q) {
+        if ((bits >> q) & 1u) nxt = s0 + q;
+        rows_q[q] = nxt == INT_MAX ? c1.x : c0.x + sc.endrow[nxt];
+      }
+      int m0 = 0, m1 = 0;
+      int64_t xb0 = 0;
+      if constexpr (XB && DVALS) {
+        m0 = __ldg(sm + k);
+        m1 = __ldg(sm + k + 1);
+        xb0 = __ldg(a.vec_base + m0);
+      }
 #pragma unroll
       for (int q = 0; q < IPT; ++q) {
         const int l = s0 + q - off;
-        c[q] = (unsigned)l < (unsigned)nnz ? ld_stream(a.atoms.idx + j0 + l) : 0;
-      }
-    }
-    const int e_pre = lane < nrows ? __ldg(a.rp + c0.x + 1 + lane) : 0;
-    warp_row_pass<IPT, false>(a.rp, c0.x, nrows, j0, off, 0.f, e_pre, sc);
-    __syncwarp();
-    const unsigned bits = (sc.bits[s0 >> 5] >> (s0 & 31)) & (IPT == 32 ? 0xffffffffu : ((1u << IPT) - 1u));
-    // first marked slot of each later lane: suffix minimum over the lanes
-    int fm = bits ? s0 + __ffs(bits) - 1 : INT_MAX;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int n = __shfl_down_sync(kFull, fm, o);
-      if (lane + o < 32) fm = min(fm, n);
-    }
-    int nxt = __shfl_down_sync(kFull, fm, 1);
-    if (lane == 31) nxt = INT_MAX;
-    int rows_q[IPT];
-#pragma unroll
-    for (int q = IPT - 1; q >= 0; --q) {
-      if ((bits >> q) & 1u) nxt = s0 + q;
-      rows_q[q] = nxt == INT_MAX ? c1.x : c0.x + sc.endrow[nxt];
-    }
-    int m0 = 0, m1 = 0;
-    int64_t xb0 = 0;
-    if constexpr (XB && DVALS) {
-      m0 = __ldg(sm + k);
-      m1 = __ldg(sm + k + 1);
-      xb0 = __ldg(a.vec_base + m0);
-    }
-#pragma unroll
-    for (int q = 0; q < IPT; ++q) {
-      const int l = s0 + q - off;
-      if ((unsigned)l < (unsigned)nnz) {
-        const int64_t j = (int64_t)j0 + l;
-        if constexpr (DVALS) {
-          const float xv = a.atoms.gather(c[q], atom_xbase<XB>(a, m0, m1, xb0, j));
-          __stcs(a.dvals + j, __fmul_rn(__ldg(a.dy + rows_q[q]), xv));
-        } else {
-          a.tile_of_atom[j] = rows_q[q];
+        if ((unsigned)l < (unsigned)nnz) {
+          const int64_t j = (int64_t)j0 + l;
+          if constexpr (DVALS) {
+            const float xv = a.atoms.gather(c[q], atom_xbase<XB>(a, m0, m1, xb0, j));
+            __stcs(a.dvals + j, __fmul_rn(__ldg(a.dy + rows_q[q]), xv));
+          } else {
+            a.tile_of_atom[j] = rows_q[q];
+          }
         }
       }
+      __syncwarp();
+      if (lane < IPT) sc.bits[lane] = 0u;
+      __syncwarp();
+      c0 = c1;
     }
-    __syncwarp();
-    if (lane < IPT) sc.bits[lane] = 0u;
-    __syncwarp();
-    c0 = c1;
-  }
-  if (dynamic) {
-    if (threadIdx.x == 0) s_unit[it & 1] = (int)gridDim.x + (int)atomicAdd(a.ticket + 1, 1u);
-    __syncthreads();
-    u = s_unit[it & 1];
+  };
+  bool dynamic;
+  if (a.share_ent) {
+    // guided shares of the look-back table, taken by each warp from the counter
+    dynamic = true;
+    const int S = a.num_workers;
+    int sh = 0;
+    if (lane == 0) sh = (int)atomicAdd(a.ticket + 1, 1u);
+    sh = __shfl_sync(kFull, sh, 0);
+    while (sh < S) {
+      const int64_t b0 = __ldg(a.share_ent + sh);
+      const int nt = (int)(__ldg(a.share_ent + sh + 1) - b0) - 1;
+      expand_share(a.splits + b0, XB ? a.split_m + b0 : nullptr, nt);
+      if (lane == 0) sh = (int)atomicAdd(a.ticket + 1, 1u);
+      sh = __shfl_sync(kFull, sh, 0);
+    }
   } else {
-    u = nunits;
+    const int nwaves = a.waves ? a.num_waves : 1;
+    const int upw = a.num_workers / WPB;
+    const int nunits = nwaves * upw;
+    // work units as in mp_spmv_warp_kernel, taken in order when there are more
+    // than CTAs
+    dynamic = nunits > (int)gridDim.x;
+    int u = blockIdx.x;
+    for (int it = 0; u < nunits; ++it) {
+      const int wave = u / upw;
+      const int w = (u - wave * upw) * WPB + warp;
+      int64_t ebase = 0;
+      int tpc = a.tiles_per_cta;
+      if (a.waves) {
+        ebase = a.waves[wave].entry_base;
+        tpc = a.waves[wave].tpc;
+      }
+      const int2* sp = a.splits + (size_t)ebase + (size_t)w * (tpc + 1);
+      const int32_t* sm = XB ? a.split_m + (size_t)ebase + (size_t)w * (tpc + 1) : nullptr;
+      const int2 t0 = __ldg(sp);
+      const int2 e1 = __ldg(sp + tpc);
+      const int64_t share = (int64_t)(e1.x - t0.x) + (e1.y - t0.y);
+      expand_share(sp, sm, (int)((share + a.items_per_tile - 1) / a.items_per_tile));
+      if (dynamic) {
+        if (threadIdx.x == 0) s_unit[it & 1] = (int)gridDim.x + (int)atomicAdd(a.ticket + 1, 1u);
+        __syncthreads();
+        u = s_unit[it & 1];
+      } else {
+        u = nunits;
+      }
+    }
   }
-  }  // units
-  // the last CTA to finish resets the unit counter for the next launch
+  // the last CTA to finish resets the counter for the next launch
   if (dynamic && cta_ticket(a, &s_last) && threadIdx.x == 0) {
     a.ticket[0] = 0u;
     a.ticket[1] = 0u;

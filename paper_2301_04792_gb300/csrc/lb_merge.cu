@@ -18,6 +18,12 @@ void MpTable::release() {
   cudaFree(carry_val);
   cudaFree(carry_row);
   cudaFree(ticket);
+  cudaFree(share_ent);
+  cudaFree(share_head);
+  cudaFree(records);
+  share_ent = nullptr;
+  share_head = nullptr;
+  records = nullptr;
   splits = nullptr;
   d_diag = nullptr;
   split_m = nullptr;
@@ -83,6 +89,27 @@ static void* expand_fn() {
 template <int IPT, bool XB, bool PERM, bool VEC>
 static void* warp_fn() {
   return reinterpret_cast<void*>(lbk::mp_spmv_warp_kernel<IPT, XB, PERM, VEC>);
+}
+template <int IPT, bool XB, bool PERM, bool VEC>
+static void* lookback_fn() {
+  return reinterpret_cast<void*>(lbk::mp_spmv_lookback_kernel<IPT, XB, PERM, VEC>);
+}
+template <int IPT>
+static void* pick_lookback(bool xb, bool perm, bool vec) {
+  if (vec) {
+    if (xb) return perm ? lookback_fn<IPT, true, true, true>() : lookback_fn<IPT, true, false, true>();
+    return perm ? lookback_fn<IPT, false, true, true>() : lookback_fn<IPT, false, false, true>();
+  }
+  if (xb) return perm ? lookback_fn<IPT, true, true, false>() : lookback_fn<IPT, true, false, false>();
+  return perm ? lookback_fn<IPT, false, true, false>() : lookback_fn<IPT, false, false, false>();
+}
+static void* kernel_lookback(int ipt, bool xb, bool perm, bool vec) {
+  switch (ipt) {
+    case 4: return pick_lookback<4>(xb, perm, vec);
+    case 8: return pick_lookback<8>(xb, perm, vec);
+    case 16: return pick_lookback<16>(xb, perm, vec);
+  }
+  return nullptr;
 }
 template <int IPT, bool XB, bool DV>
 static void* expand_warp_fn() {
@@ -179,10 +206,12 @@ static cudaError_t launch(void* fn, int grid, size_t smem, cudaStream_t s, lbk::
 }
 
 int occupancy_mp(int ipt, int variant) {
-  void* fn = variant == 0 ? kernel_warp(ipt, false, false, true)
-             : variant == 1 ? kernel_plain(ipt, false) : kernel_tma(ipt, false, false);
+  void* fn = variant == 0   ? kernel_warp(ipt, false, false, true)
+             : variant == 3 ? kernel_lookback(ipt, false, false, true)
+             : variant == 1 ? kernel_plain(ipt, false)
+                            : kernel_tma(ipt, false, false);
   if (!fn) return 1;
-  const size_t smem = variant == 0 ? 0 : variant == 1 ? plain_smem(ipt) : tma_smem(ipt);
+  const size_t smem = warp_workers(variant) ? 0 : variant == 1 ? plain_smem(ipt) : tma_smem(ipt);
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kBlock, smem) != cudaSuccess || occ < 1) occ = 1;
@@ -251,16 +280,116 @@ __global__ void split_matrix_kernel(const int2* __restrict__ splits, int64_t ent
   out[e] = lbk::find_matrix(nnz_base, 0, num - 1, (int64_t)splits[e].y);
 }
 
+// Split (i, d - i) of diagonal d: the smallest i in [max(0, d-N), min(d, R)]
+// with i == min(d, R) or rp[i+1] > d-i-1 (a row end precedes the atom with the
+// same index).
+__device__ __forceinline__ int2 merge_split(const int32_t* __restrict__ rp, int32_t R, int64_t N, int64_t d) {
+  int64_t lo = d - N > 0 ? d - N : 0;
+  int64_t hi = d < R ? d : R;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if ((int64_t)__ldg(rp + mid + 1) > d - mid - 1) hi = mid;
+    else lo = mid + 1;
+  }
+  return make_int2((int)lo, (int)(d - lo));
+}
+
+__global__ void mp_splits_at_kernel(const int32_t* __restrict__ rp, int32_t R, int64_t N,
+                                    const int64_t* __restrict__ diag, int64_t entries, int2* out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < entries) out[e] = merge_split(rp, R, N, diag[e]);
+}
+
+// first two split entries of every share (one load for a warp that opens it)
+__global__ void share_heads_kernel(const int2* __restrict__ splits, const int64_t* __restrict__ share_ent, int S,
+                                   int4* head) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= S) return;
+  const int64_t b = share_ent[q];
+  const int2 c0 = splits[b];
+  const int2 c1 = share_ent[q + 1] - b > 1 ? splits[b + 1] : c0;
+  head[q] = make_int4(c0.x, c0.y, c1.x, c1.y);
+}
+
+// The look-back table (mp_variant 3): shares of whole warp tiles in merge
+// order with guided sizes, each about half of one warp's part of the work
+// still left (rounded up to whole tiles, at least min_tiles), so shares shrink
+// from several tiles to min_tiles towards the end and the warps, taking them
+// in order, finish close together.
+static lb_status_t build_guided_table(MpTable& t, const int32_t* rp, int32_t R, int64_t N, int num_sms, int occ,
+                                      int min_tiles, const BatchBases* batch, cudaStream_t s) {
+  constexpr int kWarps = kBlock / 32;
+  const int64_t tile = t.items_per_tile;
+  int64_t ctas = (t.items + kWarps * tile - 1) / (kWarps * tile);
+  ctas = std::max<int64_t>(1, std::min<int64_t>(ctas, (int64_t)num_sms * occ));
+  t.grid = (int)ctas;
+  const int64_t P = ctas * kWarps;
+  const int64_t mt = std::max(1, min_tiles);
+  std::vector<int64_t> ent{0}, diag;
+  int64_t d = 0, max_tiles = 1;
+  while (d < t.items) {
+    const int64_t rem = t.items - d;
+    int64_t tiles = std::max(mt, (rem + 2 * P * tile - 1) / (2 * P * tile));
+    const int64_t len = std::min(rem, tiles * tile);
+    tiles = (len + tile - 1) / tile;
+    for (int64_t k = 0; k < tiles; ++k) diag.push_back(d + k * tile);
+    d += len;
+    diag.push_back(d);
+    ent.push_back(ent.back() + tiles + 1);
+    max_tiles = std::max(max_tiles, tiles);
+  }
+  if (diag.empty()) {  // no rows and no atoms: one empty share
+    diag = {0, 0};
+    ent.push_back(2);
+  }
+  const int64_t S = (int64_t)ent.size() - 1;
+  if (S >= ((int64_t)1 << 31)) {
+    set_error("merge-path: too many look-back shares");
+    return LB_ERR_UNSUPPORTED;
+  }
+  t.workers = (int)S;
+  t.tiles_per_cta = (int)max_tiles;
+  t.entries = (int64_t)diag.size();
+  t.num_waves = 1;
+  LB_CUDA_TRY(cudaMalloc(&t.splits, sizeof(int2) * (size_t)t.entries));
+  LB_CUDA_TRY(cudaMalloc(&t.d_diag, sizeof(int64_t) * (size_t)t.entries));
+  LB_CUDA_TRY(cudaMalloc(&t.share_ent, sizeof(int64_t) * (size_t)(S + 1)));
+  LB_CUDA_TRY(cudaMalloc(&t.share_head, sizeof(int4) * (size_t)S));
+  LB_CUDA_TRY(cudaMalloc(&t.records, sizeof(unsigned long long) * (size_t)S));
+  LB_CUDA_TRY(cudaMalloc(&t.ticket, sizeof(unsigned) * 4));
+  LB_CUDA_TRY(cudaMemcpyAsync(t.d_diag, diag.data(), sizeof(int64_t) * diag.size(), cudaMemcpyHostToDevice, s));
+  LB_CUDA_TRY(cudaMemcpyAsync(t.share_ent, ent.data(), sizeof(int64_t) * ent.size(), cudaMemcpyHostToDevice, s));
+  LB_CUDA_TRY(cudaMemsetAsync(t.records, 0, sizeof(unsigned long long) * (size_t)S, s));
+  // ticket, counter, epoch (records hold (epoch << 1) | FINAL; 0 = never published), spare
+  const unsigned init[4] = {0u, 0u, 1u, 0u};
+  LB_CUDA_TRY(cudaMemcpyAsync(t.ticket, init, sizeof(init), cudaMemcpyHostToDevice, s));
+  const unsigned eb = (unsigned)((t.entries + 255) / 256);
+  mp_splits_at_kernel<<<eb, 256, 0, s>>>(rp, R, N, t.d_diag, t.entries, t.splits);
+  LB_CUDA_TRY(cudaGetLastError());
+  share_heads_kernel<<<(unsigned)((S + 255) / 256), 256, 0, s>>>(t.splits, t.share_ent, (int)S, t.share_head);
+  LB_CUDA_TRY(cudaGetLastError());
+  if (batch) {
+    LB_CUDA_TRY(cudaMalloc(&t.split_m, sizeof(int32_t) * (size_t)t.entries));
+    split_matrix_kernel<<<eb, 256, 0, s>>>(t.splits, t.entries, batch->nnz_base, batch->num, t.split_m);
+    LB_CUDA_TRY(cudaGetLastError());
+  }
+  // the host vectors must outlive the copies
+  LB_CUDA_TRY(cudaStreamSynchronize(s));
+  t.built = true;
+  return LB_OK;
+}
+
 lb_status_t build_mp_table(MpTable& t, const int32_t* rp, int32_t R, int64_t N, int ipt, int variant, int num_sms,
                            int ctas_per_sm, const BatchBases* batch, cudaStream_t s, const int64_t* item_prefix,
-                           const int64_t* row_prefix, int num_mats, int wave_items, int units_per_cta) {
+                           const int64_t* row_prefix, int num_mats, int wave_items, int units_per_cta,
+                           int tiles_per_share) {
   t.release();
   if (!kernel_tma(ipt, false, false)) {
     set_error("items_per_thread must be 4, 8 or 16");
     return LB_ERR_UNSUPPORTED;
   }
-  if (variant < 0 || variant > 2) {
-    set_error("mp_variant must be 0, 1 or 2");
+  if (variant < 0 || variant > 3) {
+    set_error("mp_variant must be 0, 1, 2 or 3");
     return LB_ERR_UNSUPPORTED;
   }
   t.ipt = ipt;
@@ -285,6 +414,9 @@ lb_status_t build_mp_table(MpTable& t, const int32_t* rp, int32_t R, int64_t N, 
     const int64_t share = (t.items + t.workers - 1) / t.workers;
     int64_t tpc = (share + t.items_per_tile - 1) / t.items_per_tile;
     t.tiles_per_cta = (int)(tpc < 1 ? 1 : tpc);
+  } else if (variant == 3) {
+    t.items_per_tile = 32 * ipt - 4;
+    return build_guided_table(t, rp, R, N, num_sms, occ, tiles_per_share, batch, s);
   } else {
     // 4 items short of the CTA's thread slots: a tile's atoms start up to 3
     // slots into their 16-byte aligned window, and all of them must still fall
@@ -340,8 +472,8 @@ lb_status_t build_mp_table(MpTable& t, const int32_t* rp, int32_t R, int64_t N, 
   LB_CUDA_TRY(cudaMalloc(&t.d_diag, sizeof(int64_t) * (size_t)t.entries));
   LB_CUDA_TRY(cudaMalloc(&t.carry_val, sizeof(float) * (size_t)t.workers * nw));
   LB_CUDA_TRY(cudaMalloc(&t.carry_row, sizeof(int32_t) * (size_t)t.workers * nw));
-  LB_CUDA_TRY(cudaMalloc(&t.ticket, sizeof(unsigned) * 2));
-  LB_CUDA_TRY(cudaMemsetAsync(t.ticket, 0, sizeof(unsigned) * 2, s));
+  LB_CUDA_TRY(cudaMalloc(&t.ticket, sizeof(unsigned) * 4));
+  LB_CUDA_TRY(cudaMemsetAsync(t.ticket, 0, sizeof(unsigned) * 4, s));
   const int threads = 256;
   const unsigned blocks = (unsigned)((t.entries + threads - 1) / threads);
   if (nw > 1) {
@@ -393,6 +525,9 @@ static lbk::MpArgs make_args(const MpTable& t, const SpmvCall& c) {
   a.carry_val = t.carry_val;
   a.carry_row = t.carry_row;
   a.ticket = t.ticket;
+  a.share_ent = t.share_ent;
+  a.share_head = t.share_head;
+  a.records = t.records;
   a.waves = static_cast<const lbk::WaveDesc*>(t.d_waves);
   a.num_waves = t.num_waves;
   a.status = c.status;
@@ -420,6 +555,8 @@ lb_status_t launch_mp_spmv(const MpTable& t, const SpmvCall& c, cudaStream_t s) 
   cudaError_t e;
   if (t.variant == 0) {
     e = launch(kernel_warp(t.ipt, xb, perm, vec_atoms), t.grid, 0, s, &a);
+  } else if (t.variant == 3) {
+    e = launch(kernel_lookback(t.ipt, xb, perm, vec_atoms), t.grid, 0, s, &a);
   } else if (t.variant == 2 && vec_atoms && aligned16(c.rp)) {
     e = launch(kernel_tma(t.ipt, xb, perm), t.grid, tma_smem(t.ipt), s, &a);
   } else {
@@ -441,7 +578,7 @@ lb_status_t launch_mp_expand(const MpTable& t, const SpmvCall& c, const float* d
   a.dvals = dvals;
   a.tile_of_atom = tile_of_atom;
   const bool xb = c.batch != nullptr && dvals != nullptr;
-  if (t.variant == 0)
+  if (warp_workers(t.variant))
     LB_CUDA_TRY(launch(kernel_expand_warp(t.ipt, xb, dvals != nullptr), t.grid, 0, s, &a));
   else
     LB_CUDA_TRY(launch(kernel_expand(t.ipt, xb, dvals != nullptr), t.grid, expand_smem(t.ipt), s, &a));

@@ -105,4 +105,5 @@ def test_autotune_rejects_bad_args_before_any_launch(lib):
                            None, None) == 1
     assert b"num_cols" in lib.lb_last_error()
     assert plan.value is None
+    assert ctypes.sizeof(_lib.PlanOpts) == 12 * 4
     assert ctypes.sizeof(_lib.TuneResult) == 5 * 4 + ctypes.sizeof(_lib.PlanOpts) + 20 * 36

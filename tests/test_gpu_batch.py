@@ -40,7 +40,7 @@ def make_plan(lb, b, **kw):
     return plan, rp_cat, ci, v
 
 
-def check_batch(lb, b, ipts=(8,), variants=(0, 1, 2), wave_items=0, units=0):
+def check_batch(lb, b, ipts=(8,), variants=(0, 1, 2, 3), wave_items=0, units=0):
     import torch
     xs, dys = batch_inputs(b)
     y64, yb, dx64, dxb, dv32 = oracle_batch(b, xs, dys)

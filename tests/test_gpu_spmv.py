@@ -26,7 +26,10 @@ SCHEDULES = [("thread_mapped", {}), ("warp_mapped", {}), ("block_mapped", {}),
              ("merge_path", {"items_per_thread": 8, "mp_variant": 2}),
              ("merge_path", {"items_per_thread": 16, "mp_variant": 2}),
              ("merge_path", {"items_per_thread": 8, "units_per_cta": 4}),
-             ("merge_path", {"items_per_thread": 4, "units_per_cta": 16})]
+             ("merge_path", {"items_per_thread": 4, "units_per_cta": 16}),
+             ("merge_path", {"items_per_thread": 8, "mp_variant": 3}),
+             ("merge_path", {"items_per_thread": 4, "mp_variant": 3, "tiles_per_share": 3}),
+             ("merge_path", {"items_per_thread": 16, "mp_variant": 3, "tiles_per_share": 2})]
 SCHED_IDS = [s + "".join(f"_{k}{v}" for k, v in o.items()) for s, o in SCHEDULES]
 
 
@@ -112,16 +115,22 @@ def test_unaligned_buffers_take_scalar_path(lbmod):
 
 def test_merge_path_splits_bit_exact(lbmod):
     for name, m in small_cases() + edge_cases():
-        for ipt, var in ((4, 0), (8, 0), (16, 0), (8, 1), (4, 2), (16, 2)):
+        for ipt, var in ((4, 0), (8, 0), (16, 0), (8, 1), (4, 2), (16, 2), (8, 3)):
             rp = to_dev(m.rp)[0]
             plan = lbmod.Plan(rp, m.nnz, "merge_path", items_per_thread=ipt, mp_variant=var)
             diag, ij = plan.splits()
             info = plan.info()
             R, N = m.num_rows, m.nnz
-            # the plan's diagonals follow the documented layout
-            d_host, tpc = lbmod.merge_diagonals(R + N, info["num_workers"], info["items_per_tile"])
-            assert tpc == info["tiles_per_cta"]
-            assert np.array_equal(diag, d_host), name
+            if var == 3:
+                # guided shares: tiles of items_per_tile items in order, each share ending where
+                # the next begins, the last at R + N
+                assert diag[0] == 0 and diag[-1] == R + N and (np.diff(diag) >= 0).all()
+                assert (np.diff(diag) <= info["items_per_tile"]).all()
+            else:
+                # the plan's diagonals follow the documented layout
+                d_host, tpc = lbmod.merge_diagonals(R + N, info["num_workers"], info["items_per_tile"])
+                assert tpc == info["tiles_per_cta"]
+                assert np.array_equal(diag, d_host), name
             assert np.array_equal(ij, oracle.merge_splits(diag, m.rp)), f"{name} ipt={ipt}"
 
 
@@ -232,3 +241,22 @@ def test_full_rmat_and_stencil(lbmod):
     m = W.stencil27()
     assert m.nnz == 109_215_352
     full_size_check(lbmod, m, W.x_for(m), sched)
+
+
+def test_lookback_rows_spanning_many_shares(lbmod):
+    """Variant 3 with one-tile shares: rows of 50,000 and 70,000 atoms span hundreds
+    of shares, so the look-back walks many 32-share windows; repeated runs are
+    bit-identical."""
+    import torch
+    m = W.from_lengths(np.array([50_000, 3, 0, 70_000, 1, 0, 0, 40, 5000]), 120_000, seed=8)
+    x = W.x_for(m)
+    y64, b = oracle.spmv(m.rp, m.ci, m.v, x)
+    rp, ci, v, xd = to_dev(m.rp, m.ci, m.v, x)
+    for ipt in (4, 8):
+        plan = lbmod.Plan(rp, m.nnz, "merge_path", items_per_thread=ipt, mp_variant=3, tiles_per_share=1)
+        assert plan.info()["num_workers"] >= m.nnz // (32 * ipt)
+        ys = [plan.spmv(ci, v, xd) for _ in range(3)]
+        assert_within_bound(ys[0].cpu().numpy(), y64, b, f"lookback ipt={ipt}")
+        for y in ys[1:]:
+            assert torch.equal(y.view(torch.int32), ys[0].view(torch.int32))
+        plan.status()
