@@ -247,7 +247,8 @@ lb_status_t lb_spmv_noalloc(const int32_t* tile_offsets, int32_t num_tiles, int3
  *
  * Candidate families (bits of lb_tune_opts_t.families; 0 = all):
  *   LB_TUNE_MP_WARP  merge-path, warp workers, items_per_thread 4, 8, 16 with one static unit
- *                    per CTA, and items_per_thread 8 with 4 and 8 dynamic units per CTA
+ *                    per CTA, items_per_thread 8 with 4 and 8 dynamic units per CTA, and the
+ *                    look-back form (variant 3) with items_per_thread 8 and 4
  *   LB_TUNE_MP_CTA   merge-path, CTA workers: per-thread search (variant 1) and
  *                    bulk-copy ring (variant 2, only for 16-byte aligned buffers),
  *                    items_per_thread 4 and 8

@@ -58,6 +58,7 @@ std::vector<Candidate> candidate_list(lb_schedule_t prior, int families, bool al
   if (families & LB_TUNE_MP_WARP) {
     for (int ipt : {8, 4, 16}) v.push_back({LB_MERGE_PATH, ipt, 0, 0});
     for (int units : {4, 8}) v.push_back({LB_MERGE_PATH, 8, 0, 0, units});
+    for (int ipt : {8, 4}) v.push_back({LB_MERGE_PATH, ipt, 0, 3});
   }
   if (families & LB_TUNE_MP_CTA) {
     for (int ipt : {4, 8}) v.push_back({LB_MERGE_PATH, ipt, 0, 1});

@@ -196,6 +196,7 @@ struct MpArgs {
   int items_per_tile;
   int32_t num_tiles;
   int64_t num_atoms;         // length of the atom arrays (bounds of vector loads)
+  int32_t num_entries;       // split-table entries
   const WaveDesc* waves;    // batched tables: the waves in order; nullptr = one wave
   int num_waves;
   float* carry_val;         // [num_waves x num_ctas], one slot per work unit
@@ -1180,51 +1181,66 @@ __global__ void __launch_bounds__(256, IPT <= 8 ? 4 : 2) mp_spmv_lookback_kernel
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   WarpWalker<IPT, XB, PERM, VEC> wk(a, sc_all[warp]);
   const unsigned epoch = *reinterpret_cast<volatile unsigned*>(a.ticket + 2);
-  const int S = a.num_workers;
-  bool ok = true;
+  // the first row of share p (still needing its predecessors' sums) gets them
+  auto resolve = [&](int p) {
+    float total;
+    if (!look_back(a.records, p, epoch, total) && lane == 0 && a.status) atomicOr(a.status, kDevErrTimeout);
+    if (lane == 0) {
+      float* py = a.out + __ldg(&a.share_head[p].x);
+      __stcg(py, __ldcg(py) + total);
+    }
+  };
 
   int s = 0;
   if (lane == 0) s = (int)atomicAdd(a.ticket + 1, 1u);
   s = __shfl_sync(kFull, s, 0);
-  // state of share s (split entries < 2^31: the plan checks)
-  int base = 0;
-  int ntiles = 0;
-  int2 c_start = make_int2(0, 0), c0 = c_start, c1 = c_start;
+  // the current tile starts at split entry e (e_last: the share's last tile)
+  int e = 0, e_last = 0;
+  int2 c0 = make_int2(0, 0), c1 = c0;
   int c_cur[IPT], vb_cur[IPT];
   int e_cur = 0;
-  if (s < S) {
-    base = (int)__ldg(a.share_ent + s);
-    ntiles = (int)__ldg(a.share_ent + s + 1) - base - 1;
+  if (s < a.num_workers) {
+    e = (int)__ldg(a.share_ent + s);
+    e_last = (int)__ldg(a.share_ent + s + 1) - 2;
     const int4 h = __ldg(a.share_head + s);
-    c_start = c0 = make_int2(h.x, h.y);
+    c0 = make_int2(h.x, h.y);
     c1 = make_int2(h.z, h.w);
     wk.load_atoms(c0, c1, c_cur, vb_cur);
     e_cur = wk.load_ends(c0, c1);
   }
-  WarpSplits spl{a.splits + base, ntiles + 1};
+  // split entries, 32 at a time in lane registers, by absolute index
+  int chunk = -1;
+  int2 creg = make_int2(0, 0);
+  auto split_at = [&](int i) {
+    if ((i >> 5) != chunk) {
+      chunk = i >> 5;
+      const int idx = (chunk << 5) + lane;
+      creg = idx < a.num_entries ? __ldg(a.splits + idx) : make_int2(0, 0);
+    }
+    return make_int2(__shfl_sync(kFull, creg.x, i & 31), __shfl_sync(kFull, creg.y, i & 31));
+  };
   float carry = 0.f;
-  int k = 0;
-  int next = S;          // lane 0: the share after s
+  int next = 0;         // lane 0: the share after s, taken two tiles before its end
   bool taken = false;
-  int pend_s = -1, pend_row = 0;  // share whose first row still needs its predecessors' sums
-  while (s < S) {
-    if (!taken && k + 2 >= ntiles) {
+  int pend = -1;        // share whose first row still needs its predecessors' sums
+  while (s < a.num_workers) {
+    if (!taken && e + 1 >= e_last) {
       if (lane == 0) next = (int)atomicAdd(a.ticket + 1, 1u);
       taken = true;
     }
     float xg[IPT], vv[IPT];
-    wk.gather_tile(XB ? a.split_m + (base + k) : nullptr, c0, c1, c_cur, vb_cur, xg, vv);
-    const bool last = k + 1 == ntiles;
+    wk.gather_tile(XB ? a.split_m + e : nullptr, c0, c1, c_cur, vb_cur, xg, vv);
+    const bool last = e == e_last;
     int2 c2 = c1;
     int e_next = 0;
-    int sn = S;
+    int sn = 0;
     if (!last) {
-      c2 = spl.get(k + 2);
+      c2 = split_at(e + 2);
       wk.load_atoms(c1, c2, c_cur, vb_cur);
       e_next = wk.load_ends(c1, c2);
     } else {
       sn = __shfl_sync(kFull, next, 0);
-      if (sn < S) {
+      if (sn < a.num_workers) {
         const int4 hn = __ldg(a.share_head + sn);
         wk.load_atoms(make_int2(hn.x, hn.y), make_int2(hn.z, hn.w), c_cur, vb_cur);
         e_next = wk.load_ends(make_int2(hn.x, hn.y), make_int2(hn.z, hn.w));
@@ -1235,46 +1251,28 @@ __global__ void __launch_bounds__(256, IPT <= 8 ? 4 : 2) mp_spmv_lookback_kernel
     if (!last) {
       c0 = c1;
       c1 = c2;
-      ++k;
+      ++e;
       continue;
     }
-    // share s is done; c1 is its end
-    const bool has_end = c1.x > c_start.x;
-    if (lane == 0 && s + 1 < S) publish_record(a.records + s, epoch, has_end, carry);
-    if (pend_s >= 0) {
-      float total;
-      ok = look_back(a.records, pend_s, epoch, total) && ok;
-      if (lane == 0) {
-        float* py = a.out + pend_row;
-        __stcg(py, __ldcg(py) + total);
-      }
-    }
-    pend_s = (has_end && s > 0) ? s : -1;
-    pend_row = c_start.x;
-    // on to share sn, its first tile already loading (its head and entry
-    // base are read again: cached since the loads above)
+    // share s is done; c1 is its end, its head holds its first row
+    const bool has_end = c1.x > __ldg(&a.share_head[s].x);
+    if (lane == 0 && s + 1 < a.num_workers) publish_record(a.records + s, epoch, has_end, carry);
+    if (pend >= 0) resolve(pend);
+    pend = (has_end && s > 0) ? s : -1;
+    // on to share sn, its first tile already loading (head and entry base
+    // read again: cached since the loads above)
     s = sn;
-    if (s < S) {
-      base = (int)__ldg(a.share_ent + s);
-      ntiles = (int)__ldg(a.share_ent + s + 1) - base - 1;
+    if (s < a.num_workers) {
+      e = (int)__ldg(a.share_ent + s);
+      e_last = (int)__ldg(a.share_ent + s + 1) - 2;
       const int4 hn = __ldg(a.share_head + s);
-      c_start = c0 = make_int2(hn.x, hn.y);
+      c0 = make_int2(hn.x, hn.y);
       c1 = make_int2(hn.z, hn.w);
     }
-    spl = WarpSplits{a.splits + base, ntiles + 1};
     carry = 0.f;
-    k = 0;
     taken = false;
   }
-  if (pend_s >= 0) {
-    float total;
-    ok = look_back(a.records, pend_s, epoch, total) && ok;
-    if (lane == 0) {
-      float* py = a.out + pend_row;
-      __stcg(py, __ldcg(py) + total);
-    }
-  }
-  if (!ok && lane == 0 && a.status) atomicOr(a.status, kDevErrTimeout);
+  if (pend >= 0) resolve(pend);
   // the last CTA to finish resets the share counter and advances the epoch
   if (cta_ticket(a, &s_last) && threadIdx.x == 0) {
     const unsigned e1 = (epoch + 1u) & 0x7fffffffu;

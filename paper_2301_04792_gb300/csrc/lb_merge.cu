@@ -343,8 +343,8 @@ static lb_status_t build_guided_table(MpTable& t, const int32_t* rp, int32_t R, 
     ent.push_back(2);
   }
   const int64_t S = (int64_t)ent.size() - 1;
-  if (S >= ((int64_t)1 << 31)) {
-    set_error("merge-path: too many look-back shares");
+  if ((int64_t)diag.size() >= ((int64_t)1 << 31)) {  // the kernel indexes split entries with int
+    set_error("merge-path: too many look-back split entries");
     return LB_ERR_UNSUPPORTED;
   }
   t.workers = (int)S;
@@ -525,6 +525,7 @@ static lbk::MpArgs make_args(const MpTable& t, const SpmvCall& c) {
   a.carry_val = t.carry_val;
   a.carry_row = t.carry_row;
   a.ticket = t.ticket;
+  a.num_entries = (int32_t)t.entries;
   a.share_ent = t.share_ent;
   a.share_head = t.share_head;
   a.records = t.records;
