@@ -247,50 +247,49 @@ def bench_batched(torch, lb, W, device, reps=5):
     y = torch.empty(R, device=device)
     dx = torch.empty(C, device=device)
     dv = torch.empty(N, device=device)
-    # plain: one plan per matrix, views into the same buffers
+    # plain: one plan per matrix, views into the same buffers; two per-matrix
+    # configurations are timed (the library default, and the kernel the batch
+    # uses) and the faster one is the baseline
     rb = np.concatenate([[0], np.cumsum(rows)])
     cb = np.concatenate([[0], np.cumsum(cols)])
     nb = np.concatenate([[0], np.cumsum(nnz)])
-    plans = []
-    for mi in range(b.num):
-        rpm = rp_cat[rb[mi] + mi: rb[mi + 1] + mi + 1]
-        p = lb.Plan(rpm, int(nnz[mi]), "merge_path", num_cols=int(cols[mi]))
-        p.prepare_backward(int(cols[mi]), ci[nb[mi]:nb[mi + 1]])
-        plans.append((p, slice(rb[mi], rb[mi + 1]), slice(cb[mi], cb[mi + 1]), slice(nb[mi], nb[mi + 1]),
-                      int(cols[mi])))
-
-    # raw C-ABI calls with precomputed pointers, so host overhead does not favour the batch
     import ctypes
     from paper_2301_04792_gb300 import _lib
     lib = _lib.load()
     vp = ctypes.c_void_p
     f4, i4 = 4, 4
 
-    calls_list = []
-
-    def plain_calls(stream_ptr):
+    def make_plain(**kw):
+        plans = []
+        for mi in range(b.num):
+            rpm = rp_cat[rb[mi] + mi: rb[mi + 1] + mi + 1]
+            p = lb.Plan(rpm, int(nnz[mi]), "merge_path", num_cols=int(cols[mi]), **kw)
+            p.prepare_backward(int(cols[mi]), ci[nb[mi]:nb[mi + 1]])
+            plans.append(p)
+        # raw C-ABI calls with precomputed pointers, so host overhead does not favour the batch
         calls = []
-        for p, rs, cs, ns, cm in plans:
-            civ = vp(ci.data_ptr() + i4 * int(ns.start))
-            vv = vp(v.data_ptr() + f4 * int(ns.start))
-            xv = vp(x.data_ptr() + f4 * int(cs.start))
-            yv = vp(y.data_ptr() + f4 * int(rs.start))
-            dyv = vp(dy.data_ptr() + f4 * int(rs.start))
-            dxv = vp(dx.data_ptr() + f4 * int(cs.start))
-            dvv = vp(dv.data_ptr() + f4 * int(ns.start))
-            calls.append((p.handle, civ, vv, xv, yv, dyv, dxv, dvv, cm))
-        calls_list[:] = calls
-        sp_ = vp(stream_ptr)
+        for mi, p in enumerate(plans):
+            calls.append((p.handle, vp(ci.data_ptr() + i4 * int(nb[mi])), vp(v.data_ptr() + f4 * int(nb[mi])),
+                          vp(x.data_ptr() + f4 * int(cb[mi])), vp(y.data_ptr() + f4 * int(rb[mi])),
+                          vp(dy.data_ptr() + f4 * int(rb[mi])), vp(dx.data_ptr() + f4 * int(cb[mi])),
+                          vp(dv.data_ptr() + f4 * int(nb[mi])), int(cols[mi])))
 
-        def run():
-            for h, civ, vv, xv, yv, dyv, dxv, dvv, cm in calls:
-                _lib.check(lib.lb_spmv(h, civ, vv, xv, yv, sp_), "lb_spmv")
-                _lib.check(lib.lb_spmv_backward(h, cm, civ, vv, xv, dyv, dxv, dvv, sp_), "lb_spmv_backward")
-        return run
+        def runner(stream_ptr):
+            sp_ = vp(stream_ptr)
 
-    plain_step = plain_calls(torch.cuda.current_stream(device).cuda_stream)
+            def run():
+                for h, civ, vv, xv, yv, dyv, dxv, dvv, cm in calls:
+                    _lib.check(lib.lb_spmv(h, civ, vv, xv, yv, sp_), "lb_spmv")
+                    _lib.check(lib.lb_spmv_backward(h, cm, civ, vv, xv, dyv, dxv, dvv, sp_), "lb_spmv_backward")
+            return run
+        return plans, calls, runner
 
-    bp = lb.BatchPlan(rows, cols, nnz, rp_cat)
+    plain_cfgs = {"merge_path_ipt8_v0": dict(items_per_thread=8, mp_variant=0),
+                  "merge_path_ipt4_v3": dict(items_per_thread=4, mp_variant=3)}
+    plains = {k: make_plain(**kw) for k, kw in plain_cfgs.items()}
+
+    # the batch: look-back shares (variant 3), items_per_thread 4 for both tile sets
+    bp = lb.BatchPlan(rows, cols, nnz, rp_cat, mp_variant=3, items_per_thread=4)
     bp.prepare_backward(ci)
 
     def batched_step():
@@ -306,15 +305,10 @@ def bench_batched(torch, lb, W, device, reps=5):
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g):
         batched_step()
-    # the same per-matrix launches captured in a graph too (removes host launch cost from "plain")
-    gp = torch.cuda.CUDAGraph()
-    cap = torch.cuda.Stream(device=device)
-    with torch.cuda.graph(gp, stream=cap):
-        plain_calls(cap.cuda_stream)()
     for _ in range(3):
-        plain_step()
         g.replay()
-        gp.replay()
+        for _, _, runner in plains.values():
+            runner(torch.cuda.current_stream(device).cuda_stream)()
     torch.cuda.synchronize()
 
     def timed(fn):
@@ -328,9 +322,19 @@ def bench_batched(torch, lb, W, device, reps=5):
             ts.append(e0.elapsed_time(e1))
         return statistics.median(ts)
 
-    t_plain = timed(plain_step)
-    t_plain_graph = timed(gp.replay)
     t_batch = timed(g.replay)
+    t_plains = {k: timed(r(torch.cuda.current_stream(device).cuda_stream)) for k, (_, _, r) in plains.items()}
+    best = min(t_plains, key=t_plains.get)
+    t_plain = t_plains[best]
+    _, calls_list, runner = plains[best]
+    # the faster per-matrix configuration's launches captured in a graph too (no host launch cost)
+    gp = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream(device=device)
+    with torch.cuda.graph(gp, stream=cap):
+        runner(cap.cuda_stream)()
+    gp.replay()
+    torch.cuda.synchronize()
+    t_plain_graph = timed(gp.replay)
     # the three passes on their own (batched launch vs. the 64 per-matrix launches)
     parts = {}
     for name, bfn, pfn in (
@@ -350,14 +354,17 @@ def bench_batched(torch, lb, W, device, reps=5):
     bwd_dv = 8 * N + 4 * (R + b.num) + 4 * R + 4 * C
     byts = fwd + bwd_dx + bwd_dv
     out = {"workload": f"{b.num} power-law matrices 2^20 x 2^20, ~16M nnz each (total {N} nnz)",
+           "batch_plan": "merge_path_ipt4_v3 (look-back shares), one launch per pass, CUDA graph",
+           "plain_ms_by_config": {k: round(t, 4) for k, t in t_plains.items()}, "plain_config": best,
            "plain_ms": round(t_plain, 4), "batched_graph_ms": round(t_batch, 4),
            "speedup": round(t_plain / t_batch, 4), "plain_graph_ms": round(t_plain_graph, 4),
            "speedup_vs_plain_graph": round(t_plain_graph / t_batch, 4),
            "plain_launches": 3 * b.num, "batched_launches": 3, "parts": parts,
            "fwd_bwd_bytes": byts, "batched_GBps": round(byts / (t_batch * 1e-3) / 1e9, 2),
            "plain_GBps": round(byts / (t_plain * 1e-3) / 1e9, 2)}
-    for p, *_ in plans:
-        p.close()
+    for plans_k, _, _ in plains.values():
+        for p in plans_k:
+            p.close()
     bp.close()
     del g, gp
     torch.cuda.synchronize()

@@ -98,7 +98,9 @@ typedef struct lb_plan_opts_t {
                                so more units pay off only where warps' times vary a lot, e.g. R-MAT);
                                0 or 1 = one static unit per CTA */
   int32_t tiles_per_share;  /* merge-path variant 3: smallest look-back share in warp tiles (default 1) */
-  int32_t reserved[3];
+  int32_t items_per_thread_t; /* merge-path: items_per_thread of the transposed tile set (dx) built by
+                               lb_prepare_backward / lb_batch_prepare_backward (0 = items_per_thread) */
+  int32_t reserved[2];
 } lb_plan_opts_t;
 
 /* What a plan resolved to (for tests, the autotuner and reporting). */

@@ -28,7 +28,8 @@ class PlanOpts(ctypes.Structure):
     _fields_ = [("num_cols", ctypes.c_int32), ("items_per_thread", ctypes.c_int32), ("group_size", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("validate", ctypes.c_int32), ("mp_variant", ctypes.c_int32),
                 ("wave_items", ctypes.c_int32), ("units_per_cta", ctypes.c_int32),
-                ("tiles_per_share", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("tiles_per_share", ctypes.c_int32), ("items_per_thread_t", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class PlanInfo(ctypes.Structure):

@@ -91,6 +91,7 @@ static lb_plan_opts_t defaults(const lb_plan_opts_t* o) {
   if (d.group_size == 0) d.group_size = 32;
   if (d.units_per_cta == 0) d.units_per_cta = 1;
   if (d.tiles_per_share == 0) d.tiles_per_share = 1;
+  if (d.items_per_thread_t == 0) d.items_per_thread_t = d.items_per_thread;
   return d;
 }
 
@@ -186,8 +187,9 @@ lb_status_t lb_plan_ex(lb_plan_t* out, const int32_t* tile_offsets, int32_t num_
     return LB_ERR_INVALID_ARG;
   }
   const lb_plan_opts_t o = defaults(opts);
-  if (o.items_per_thread != 4 && o.items_per_thread != 8 && o.items_per_thread != 16) {
-    set_error("lb_plan: items_per_thread must be 4, 8 or 16");
+  auto ipt_ok = [](int v) { return v == 4 || v == 8 || v == 16; };
+  if (!ipt_ok(o.items_per_thread) || !ipt_ok(o.items_per_thread_t)) {
+    set_error("lb_plan: items_per_thread and items_per_thread_t must be 4, 8 or 16");
     return LB_ERR_UNSUPPORTED;
   }
   if (o.num_cols < 0 || o.ctas_per_sm < 0) {
@@ -387,7 +389,7 @@ lb_status_t lb_prepare_backward(lb_plan_t p, int32_t num_cols, const int32_t* co
     free_transpose(p);
     return st;
   }
-  st = build_mp_table(p->mp_t, p->cp, num_cols, N, p->opts.items_per_thread, p->opts.mp_variant, p->num_sms,
+  st = build_mp_table(p->mp_t, p->cp, num_cols, N, p->opts.items_per_thread_t, p->opts.mp_variant, p->num_sms,
                       p->opts.ctas_per_sm, nullptr, s, nullptr, nullptr, 0, 0, p->opts.units_per_cta,
                       p->opts.tiles_per_share);
   if (st != LB_OK) {

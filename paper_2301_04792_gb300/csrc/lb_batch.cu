@@ -112,8 +112,10 @@ lb_status_t lb_batch_plan(lb_plan_t* out, int32_t num_mats, const int32_t* host_
   if (o.items_per_thread == 0) o.items_per_thread = 8;
   if (o.units_per_cta == 0) o.units_per_cta = 1;
   if (o.tiles_per_share == 0) o.tiles_per_share = 1;
-  if (o.items_per_thread != 4 && o.items_per_thread != 8 && o.items_per_thread != 16) {
-    set_error("lb_batch_plan: items_per_thread must be 4, 8 or 16");
+  if (o.items_per_thread_t == 0) o.items_per_thread_t = o.items_per_thread;
+  auto ipt_ok = [](int v) { return v == 4 || v == 8 || v == 16; };
+  if (!ipt_ok(o.items_per_thread) || !ipt_ok(o.items_per_thread_t)) {
+    set_error("lb_batch_plan: items_per_thread and items_per_thread_t must be 4, 8 or 16");
     return LB_ERR_UNSUPPORTED;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -237,7 +239,7 @@ lb_status_t lb_batch_prepare_backward(lb_plan_t p, const int32_t* col_cat, void*
       cudaMemcpy(hn.data(), p->bb.nnz_base, sizeof(int64_t) * (num + 1), cudaMemcpyDeviceToHost) != cudaSuccess)
     return fail(LB_ERR_CUDA, "lb_batch_prepare_backward: copy of matrix bases failed");
   for (int m = 0; m <= num; ++m) titems[m] = hc[m] + hn[m];
-  st = build_mp_table(p->mp_t, p->cp, C, N, p->opts.items_per_thread, p->opts.mp_variant, p->num_sms,
+  st = build_mp_table(p->mp_t, p->cp, C, N, p->opts.items_per_thread_t, p->opts.mp_variant, p->num_sms,
                       p->opts.ctas_per_sm, nullptr, s, titems.data(), hc.data(), num, p->opts.wave_items,
                       p->opts.units_per_cta, p->opts.tiles_per_share);
   if (st != LB_OK) return fail(st, "");

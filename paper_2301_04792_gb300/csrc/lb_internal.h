@@ -41,6 +41,7 @@ struct MpTable {
                     // 3 warp workers on dynamic shares with a look-back fix-up
   int items_per_tile = 0;
   int grid = 0;          // CTAs launched
+  int expand_grid = 0;   // variant 3: CTAs of the expand (dvals / atom tile) launches
   int workers = 0;       // owners of split-table shares (warps for variant 0, CTAs otherwise), per wave;
                          // for variant 0 workers / 8 work units per wave
   int tiles_per_cta = 0; // tiles per worker

@@ -1298,22 +1298,53 @@ __global__ void __launch_bounds__(256) mp_expand_warp_kernel(MpArgs a) {
   if (lane < IPT) sc.bits[lane] = 0u;
   __syncwarp();
   const int s0 = lane * IPT;
-  // the ntiles tiles of one share, split entries sp[0..ntiles], matrices sm
+  // the ntiles tiles of one share, split entries sp[0..ntiles], matrices sm;
+  // a tile's column indices and first row ends are loaded one tile ahead and
+  // its gathers issued before its row pass
+  auto load_cols = [&](int2 t0, int2 t1, int (&c)[IPT]) {
+    const int nnz = t1.y - t0.y, j0 = t0.y, off = j0 & 3;
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) {
+      const int l = s0 + q - off;
+      c[q] = (unsigned)l < (unsigned)nnz ? ld_stream(a.atoms.idx + j0 + l) : 0;
+    }
+  };
   auto expand_share = [&](const int2* sp, const int32_t* sm, int ntiles) {
     int2 c0 = __ldg(sp);
+    int2 c1 = ntiles > 0 ? __ldg(sp + 1) : c0;
+    int c_cur[IPT];
+    if constexpr (DVALS) {
+      if (ntiles > 0) load_cols(c0, c1, c_cur);
+    }
+    int e_cur = ntiles > 0 && lane < c1.x - c0.x ? __ldg(a.rp + c0.x + 1 + lane) : 0;
     for (int k = 0; k < ntiles; ++k) {
-      const int2 c1 = __ldg(sp + k + 1);
       const int nrows = c1.x - c0.x, nnz = c1.y - c0.y, j0 = c0.y, off = j0 & 3;
-      int c[IPT];
+      float xv[IPT];
       if constexpr (DVALS) {
+        int m0 = 0, m1 = 0;
+        int64_t xb0 = 0;
+        if constexpr (XB) {
+          m0 = __ldg(sm + k);
+          m1 = __ldg(sm + k + 1);
+          xb0 = __ldg(a.vec_base + m0);
+        }
 #pragma unroll
         for (int q = 0; q < IPT; ++q) {
           const int l = s0 + q - off;
-          c[q] = (unsigned)l < (unsigned)nnz ? ld_stream(a.atoms.idx + j0 + l) : 0;
+          xv[q] = (unsigned)l < (unsigned)nnz
+                      ? a.atoms.gather(c_cur[q], atom_xbase<XB>(a, m0, m1, xb0, (int64_t)j0 + l))
+                      : 0.f;
         }
       }
-      const int e_pre = lane < nrows ? __ldg(a.rp + c0.x + 1 + lane) : 0;
-      warp_row_pass<IPT, false>(a.rp, c0.x, nrows, j0, off, 0.f, e_pre, sc);
+      // next tile's columns and row ends, in flight while this one is expanded
+      int2 c2 = c1;
+      int e_next = 0;
+      if (k + 1 < ntiles) {
+        c2 = __ldg(sp + k + 2);
+        if constexpr (DVALS) load_cols(c1, c2, c_cur);
+        e_next = lane < c2.x - c1.x ? __ldg(a.rp + c1.x + 1 + lane) : 0;
+      }
+      warp_row_pass<IPT, false>(a.rp, c0.x, nrows, j0, off, 0.f, e_cur, sc);
       __syncwarp();
       const unsigned bits = (sc.bits[s0 >> 5] >> (s0 & 31)) & (IPT == 32 ? 0xffffffffu : ((1u << IPT) - 1u));
       // first marked slot of each later lane: suffix minimum over the lanes
@@ -1331,21 +1362,13 @@ __global__ void __launch_bounds__(256) mp_expand_warp_kernel(MpArgs a) {
         if ((bits >> q) & 1u) nxt = s0 + q;
         rows_q[q] = nxt == INT_MAX ? c1.x : c0.x + sc.endrow[nxt];
       }
-      int m0 = 0, m1 = 0;
-      int64_t xb0 = 0;
-      if constexpr (XB && DVALS) {
-        m0 = __ldg(sm + k);
-        m1 = __ldg(sm + k + 1);
-        xb0 = __ldg(a.vec_base + m0);
-      }
 #pragma unroll
       for (int q = 0; q < IPT; ++q) {
         const int l = s0 + q - off;
         if ((unsigned)l < (unsigned)nnz) {
           const int64_t j = (int64_t)j0 + l;
           if constexpr (DVALS) {
-            const float xv = a.atoms.gather(c[q], atom_xbase<XB>(a, m0, m1, xb0, j));
-            __stcs(a.dvals + j, __fmul_rn(__ldg(a.dy + rows_q[q]), xv));
+            __stcs(a.dvals + j, __fmul_rn(__ldg(a.dy + rows_q[q]), xv[q]));
           } else {
             a.tile_of_atom[j] = rows_q[q];
           }
@@ -1355,6 +1378,8 @@ __global__ void __launch_bounds__(256) mp_expand_warp_kernel(MpArgs a) {
       if (lane < IPT) sc.bits[lane] = 0u;
       __syncwarp();
       c0 = c1;
+      c1 = c2;
+      e_cur = e_next;
     }
   };
   bool dynamic;

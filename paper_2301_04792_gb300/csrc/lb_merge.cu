@@ -313,11 +313,15 @@ __global__ void share_heads_kernel(const int2* __restrict__ splits, const int64_
 
 // The look-back table (mp_variant 3): shares of whole warp tiles in merge
 // order with guided sizes, each about half of one warp's part of the work
-// still left (rounded up to whole tiles, at least min_tiles), so shares shrink
-// from several tiles to min_tiles towards the end and the warps, taking them
-// in order, finish close together.
+// still left (rounded up to whole tiles, at most max_tiles_cap, at least
+// min_tiles), so shares shrink to min_tiles towards the end and the warps,
+// taking them in order, finish close together.  For batches the cap
+// (kMaxShareTiles) keeps the shares in flight (warps x 8 tiles, about 10 M
+// items on a 152-SM GPU) within a window of the merge path, so the batch is
+// worked through in order and each matrix's vectors stay in L2 meanwhile.
+constexpr int64_t kMaxShareTiles = 8;
 static lb_status_t build_guided_table(MpTable& t, const int32_t* rp, int32_t R, int64_t N, int num_sms, int occ,
-                                      int min_tiles, const BatchBases* batch, cudaStream_t s) {
+                                      int min_tiles, int64_t max_tiles_cap, const BatchBases* batch, cudaStream_t s) {
   constexpr int kWarps = kBlock / 32;
   const int64_t tile = t.items_per_tile;
   int64_t ctas = (t.items + kWarps * tile - 1) / (kWarps * tile);
@@ -329,7 +333,8 @@ static lb_status_t build_guided_table(MpTable& t, const int32_t* rp, int32_t R, 
   int64_t d = 0, max_tiles = 1;
   while (d < t.items) {
     const int64_t rem = t.items - d;
-    int64_t tiles = std::max(mt, (rem + 2 * P * tile - 1) / (2 * P * tile));
+    int64_t tiles = std::min(max_tiles_cap, (rem + 2 * P * tile - 1) / (2 * P * tile));
+    tiles = std::max(mt, tiles);
     const int64_t len = std::min(rem, tiles * tile);
     tiles = (len + tile - 1) / tile;
     for (int64_t k = 0; k < tiles; ++k) diag.push_back(d + k * tile);
@@ -373,6 +378,12 @@ static lb_status_t build_guided_table(MpTable& t, const int32_t* rp, int32_t R, 
     split_matrix_kernel<<<eb, 256, 0, s>>>(t.splits, t.entries, batch->nnz_base, batch->num, t.split_m);
     LB_CUDA_TRY(cudaGetLastError());
   }
+  // the expand kernels take the same shares dynamically with their own occupancy
+  int occ_e = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_e, kernel_expand_warp(t.ipt, true, true), kBlock, 0) !=
+          cudaSuccess || occ_e < 1)
+    occ_e = occ;
+  t.expand_grid = (int)std::max<int64_t>(1, std::min<int64_t>((S + kWarps - 1) / kWarps, (int64_t)num_sms * occ_e));
   // the host vectors must outlive the copies
   LB_CUDA_TRY(cudaStreamSynchronize(s));
   t.built = true;
@@ -416,7 +427,10 @@ lb_status_t build_mp_table(MpTable& t, const int32_t* rp, int32_t R, int64_t N, 
     t.tiles_per_cta = (int)(tpc < 1 ? 1 : tpc);
   } else if (variant == 3) {
     t.items_per_tile = 32 * ipt - 4;
-    return build_guided_table(t, rp, R, N, num_sms, occ, tiles_per_share, batch, s);
+    // shares capped in batches only: a single matrix's dense vector stays in
+    // L2 however far apart the shares in flight are
+    return build_guided_table(t, rp, R, N, num_sms, occ, tiles_per_share, num_mats > 1 ? kMaxShareTiles : 1 << 20,
+                              batch, s);
   } else {
     // 4 items short of the CTA's thread slots: a tile's atoms start up to 3
     // slots into their 16-byte aligned window, and all of them must still fall
@@ -579,7 +593,10 @@ lb_status_t launch_mp_expand(const MpTable& t, const SpmvCall& c, const float* d
   a.dvals = dvals;
   a.tile_of_atom = tile_of_atom;
   const bool xb = c.batch != nullptr && dvals != nullptr;
-  if (warp_workers(t.variant))
+  if (t.variant == 3) {
+    a.num_ctas = t.expand_grid;
+    LB_CUDA_TRY(launch(kernel_expand_warp(t.ipt, xb, dvals != nullptr), t.expand_grid, 0, s, &a));
+  } else if (warp_workers(t.variant))
     LB_CUDA_TRY(launch(kernel_expand_warp(t.ipt, xb, dvals != nullptr), t.grid, 0, s, &a));
   else
     LB_CUDA_TRY(launch(kernel_expand(t.ipt, xb, dvals != nullptr), t.grid, expand_smem(t.ipt), s, &a));

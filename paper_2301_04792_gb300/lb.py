@@ -86,7 +86,7 @@ class Plan:
     def __init__(self, tile_offsets: torch.Tensor, num_atoms: int | None = None, schedule="merge_path",
                  num_cols: int = 0, items_per_thread: int = 0, group_size: int = 0, ctas_per_sm: int = 0,
                  validate: bool = False, mp_variant: int = 0, units_per_cta: int = 0, tiles_per_share: int = 0,
-                 stream=None):
+                 items_per_thread_t: int = 0, stream=None):
         self._lib = _lib.load()
         _need(tile_offsets, torch.int32, "tile_offsets")
         self.tile_offsets = tile_offsets
@@ -99,7 +99,8 @@ class Plan:
         self.num_cols = int(num_cols)
         opts = PlanOpts(num_cols=int(num_cols), items_per_thread=int(items_per_thread), group_size=int(group_size),
                         ctas_per_sm=int(ctas_per_sm), validate=int(bool(validate)), mp_variant=int(mp_variant),
-                        units_per_cta=int(units_per_cta), tiles_per_share=int(tiles_per_share))
+                        units_per_cta=int(units_per_cta), tiles_per_share=int(tiles_per_share),
+                        items_per_thread_t=int(items_per_thread_t))
         h = ctypes.c_void_p()
         check(self._lib.lb_plan_ex(ctypes.byref(h), _ptr(tile_offsets), self.num_tiles, self.num_atoms,
                                    int(Schedule.parse(schedule)), ctypes.byref(opts), ctypes.c_void_p(_stream(stream))),
@@ -263,7 +264,10 @@ class BatchPlan:
 
     def __init__(self, rows, cols, nnz, rp_cat: torch.Tensor, items_per_thread: int = 0, ctas_per_sm: int = 0,
                  mp_variant: int = 0, wave_items: int = 0, units_per_cta: int = 0, tiles_per_share: int = 0,
-                 stream=None):
+                 items_per_thread_t: int = 0, stream=None):
+        """mp_variant 0 walks a long batch in waves of whole matrices; mp_variant 3
+        (look-back shares, capped at 8 tiles) with items_per_thread 4 measured
+        fastest for fwd + bwd of many large matrices on GB300."""
         self._lib = _lib.load()
         _need(rp_cat, torch.int32, "rp_cat")
         self.rows = np.ascontiguousarray(rows, dtype=np.int32)
@@ -279,7 +283,7 @@ class BatchPlan:
         self.total_nnz = int(self.nnz.sum())
         opts = PlanOpts(items_per_thread=int(items_per_thread), ctas_per_sm=int(ctas_per_sm),
                         mp_variant=int(mp_variant), wave_items=int(wave_items), units_per_cta=int(units_per_cta),
-                        tiles_per_share=int(tiles_per_share))
+                        tiles_per_share=int(tiles_per_share), items_per_thread_t=int(items_per_thread_t))
         h = ctypes.c_void_p()
         check(self._lib.lb_batch_plan(ctypes.byref(h), self.rows.shape[0], self.rows.ctypes.data_as(ctypes.c_void_p),
                                       self.cols.ctypes.data_as(ctypes.c_void_p),
