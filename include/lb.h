@@ -53,7 +53,7 @@ typedef enum lb_status_t {
   LB_ERR_CUDA = 2,         /* a CUDA runtime call failed; see lb_last_error() */
   LB_ERR_OOM = 3,          /* device allocation failed */
   LB_ERR_UNSUPPORTED = 4,  /* option combination not built (e.g. group size not a power of two) */
-  LB_ERR_TIMEOUT = 5,      /* reserved: no kernel in this library waits on another block */
+  LB_ERR_TIMEOUT = 5,      /* a bounded wait gave up (look-back record or bulk-copy barrier never came) */
   LB_ERR_BAD_INPUT = 6     /* a validated kernel saw a column index outside [0, num_cols) */
 } lb_status_t;
 
@@ -374,6 +374,18 @@ lb_status_t lb_merge_diagonals(int64_t items, int32_t grid, int32_t items_per_ti
 lb_status_t lb_probe_gather(const int32_t* idx, const float* vals, const float* x, int64_t n, float* out,
                             int32_t grid, void* stream);
 int32_t lb_probe_gather_grid(void);
+/*
+ * Failure-detection self-test (no counterpart in the paper).  which = 1 runs
+ * the merge-path look-back wait against a predecessor record that is never
+ * published; which = 2 runs the bounded mbarrier wait of the bulk-copy kernel
+ * on a phase that never completes.  Either wait gives up after a few thousand
+ * polls, records the timeout in a device status word and returns; nothing
+ * faults and the context stays usable.  Returns LB_ERR_TIMEOUT when the wait
+ * gave up and reported it (the designed outcome), LB_OK if it did not,
+ * LB_ERR_INVALID_ARG for another `which`, LB_ERR_CUDA / LB_ERR_OOM on failure.
+ * Allocates 64 bytes, synchronises `stream`.
+ */
+lb_status_t lb_selftest(int32_t which, void* stream);
 
 const char* lb_status_string(lb_status_t status);
 const char* lb_last_error(void);

@@ -97,6 +97,33 @@ class Oracle:
                          _p(x, ctypes.c_float), _p(y, ctypes.c_double), _p(b, ctypes.c_double))
         return y, b
 
+    def spmv_threads(self, rp, ci, v, x, threads: int):
+        """(y64, b) as spmv, the rows cut into `threads` blocks of about equal rows + atoms,
+        each block run by or_spmv on its own host thread (ctypes releases the GIL); every
+        row is summed exactly as in spmv, so the results are identical."""
+        import threading
+        rp, ci, v, x = _c(rp, np.int32), _c(ci, np.int32), _c(v, np.float32), _c(x, np.float32)
+        R = rp.shape[0] - 1
+        y = np.empty(R, dtype=np.float64)
+        b = np.empty(R, dtype=np.float64)
+        T = max(1, min(int(threads), max(R, 1)))
+        work = rp.astype(np.int64) + np.arange(R + 1, dtype=np.int64)  # rows + atoms before each row
+        cuts = np.searchsorted(work, np.linspace(0, work[-1], T + 1), side="left").clip(0, R)
+        cuts[0], cuts[-1] = 0, R
+
+        def block(r0, r1):
+            if r1 > r0:
+                self.lib.or_spmv(int(r1 - r0), _p(rp[r0:], ctypes.c_int32), _p(ci, ctypes.c_int32),
+                                 _p(v, ctypes.c_float), _p(x, ctypes.c_float), _p(y[r0:], ctypes.c_double),
+                                 _p(b[r0:], ctypes.c_double))
+
+        ts = [threading.Thread(target=block, args=(int(cuts[t]), int(cuts[t + 1]))) for t in range(T)]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+        return y, b
+
     def spmv_rows(self, rows, rp, ci, v, x):
         """(y64, b) for the selected rows only."""
         rows = _c(rows, np.int64)
@@ -189,6 +216,10 @@ def spmv(rp, ci, v, x):
 
 def spmv_rows(rows, rp, ci, v, x):
     return default().spmv_rows(rows, rp, ci, v, x)
+
+
+def spmv_threads(rp, ci, v, x, threads: int):
+    return default().spmv_threads(rp, ci, v, x, threads)
 
 
 def merge_split(d, rp):

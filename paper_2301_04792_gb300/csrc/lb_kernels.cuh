@@ -150,10 +150,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait for a phase of `bar`: gives up after kSpinLimit polls and
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait for a phase of `bar`: gives up after `limit` polls and
 // returns false (the caller records kDevErrTimeout and winds down).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (long long n = 0; n < kSpinLimit; ++n)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit = kSpinLimit) {
+  for (long long n = 0; n < limit; ++n)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -1124,8 +1128,9 @@ __device__ __forceinline__ void publish_record(unsigned long long* rec, unsigned
 // FINAL record (or share 0) ends the run.  Waits, bounded, until every record
 // up to that one carries this launch's epoch; adds the run with a fixed
 // butterfly per window and the windows in order.  Returns false if a wait
-// gave up.
-__device__ __forceinline__ bool look_back(const unsigned long long* records, int s, unsigned epoch, float& total) {
+// gave up (after max_spins polls).
+__device__ __forceinline__ bool look_back(const unsigned long long* records, int s, unsigned epoch, float& total,
+                                          long long max_spins = kLookbackSpins) {
   const int lane = threadIdx.x & 31;
   total = 0.f;
   for (int base = s - 1; base >= 0; base -= 32) {
@@ -1143,7 +1148,7 @@ __device__ __forceinline__ bool look_back(const unsigned long long* records, int
       j = term ? __ffs(term) - 1 : 31;
       const unsigned need = (2u << j) - 1u;  // lanes 0..j
       if ((__ballot_sync(kFull, ready) & need) == need) break;
-      if (spin > kLookbackSpins) return false;
+      if (spin > max_spins) return false;
       __nanosleep(64);
     }
     float v = (lane <= j && p >= 0) ? __uint_as_float((unsigned)w) : 0.f;

@@ -107,3 +107,9 @@ def test_autotune_rejects_bad_args_before_any_launch(lib):
     assert plan.value is None
     assert ctypes.sizeof(_lib.PlanOpts) == 12 * 4
     assert ctypes.sizeof(_lib.TuneResult) == 5 * 4 + ctypes.sizeof(_lib.PlanOpts) + 20 * 36
+
+
+def test_selftest_rejects_unknown_case_without_launching(lib):
+    assert lib.lb_selftest(0, None) == 1
+    assert lib.lb_selftest(3, None) == 1
+    assert b"which" in lib.lb_last_error()

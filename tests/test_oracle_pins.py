@@ -302,3 +302,16 @@ def test_pins_reject_planted_mistakes(name):
             check(Oracle(so))
     finally:
         shutil.rmtree(d, ignore_errors=True)
+
+
+def test_threaded_oracle_runner_is_identical():
+    import workloads as W
+    """spmv_threads only splits the rows over host threads: bit-identical to spmv."""
+    for R, C, L, seed in ((0, 5, 1, 0), (1, 7, 3, 1), (37, 50, 9, 2), (5000, 3000, 40, 3)):
+        m = W.powerlaw(R, C, max(R * L // 3, 0), lmax=min(C, 200), plant_long=False, seed=seed) if R > 1 \
+            else W.from_lengths(np.full(R, min(L, C), dtype=np.int64), C, seed=seed)
+        x = W.x_for(m)
+        y, b = oracle.spmv(m.rp, m.ci, m.v, x)
+        for T in (1, 2, 7, 64):
+            yt, bt = oracle.spmv_threads(m.rp, m.ci, m.v, x, T)
+            assert np.array_equal(y.view(np.int64), yt.view(np.int64)) and np.array_equal(b, bt), (R, T)
