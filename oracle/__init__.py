@@ -56,6 +56,7 @@ def _bind(lib):
     f64p = ctypes.POINTER(ctypes.c_double)
     lib.or_spmv.argtypes = [ctypes.c_int32, i32p, i32p, f32p, f32p, f64p, f64p]
     lib.or_spmv_rows.argtypes = [ctypes.c_int64, i64p, i32p, i32p, f32p, f32p, f64p, f64p]
+    lib.or_spmm.argtypes = [ctypes.c_int32, i32p, i32p, f32p, f32p, ctypes.c_int64, ctypes.c_int32, f64p, f64p]
     lib.or_merge_split.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, i32p]
     lib.or_merge_split.restype = ctypes.c_int32
     lib.or_merge_splits.argtypes = [ctypes.c_int64, i64p, ctypes.c_int32, ctypes.c_int32, i32p, i32p]
@@ -96,6 +97,18 @@ class Oracle:
         self.lib.or_spmv(R, _p(rp, ctypes.c_int32), _p(ci, ctypes.c_int32), _p(v, ctypes.c_float),
                          _p(x, ctypes.c_float), _p(y, ctypes.c_double), _p(b, ctypes.c_double))
         return y, b
+
+    def spmm(self, rp, ci, v, B):
+        """(C64, b), both [R, K]: C = A B in FP64 for a dense row-major B [num_cols, K] and
+        b[i, j] = sum_k |v[k] B[ci[k], j]|."""
+        rp, ci, v = _c(rp, np.int32), _c(ci, np.int32), _c(v, np.float32)
+        B = _c(B, np.float32)
+        R, K = rp.shape[0] - 1, B.shape[1]
+        C = np.empty((R, K), dtype=np.float64)
+        b = np.empty((R, K), dtype=np.float64)
+        self.lib.or_spmm(R, _p(rp, ctypes.c_int32), _p(ci, ctypes.c_int32), _p(v, ctypes.c_float),
+                         _p(B, ctypes.c_float), K, K, _p(C, ctypes.c_double), _p(b, ctypes.c_double))
+        return C, b
 
     def spmv_threads(self, rp, ci, v, x, threads: int):
         """(y64, b) as spmv, the rows cut into `threads` blocks of about equal rows + atoms,
@@ -220,6 +233,10 @@ def spmv_rows(rows, rp, ci, v, x):
 
 def spmv_threads(rp, ci, v, x, threads: int):
     return default().spmv_threads(rp, ci, v, x, threads)
+
+
+def spmm(rp, ci, v, B):
+    return default().spmm(rp, ci, v, B)
 
 
 def merge_split(d, rp):

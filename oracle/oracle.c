@@ -41,6 +41,30 @@ void or_spmv(int32_t R, const int32_t* rp, const int32_t* ci, const float* v, co
 }
 
 /*
+ * C = A B for a dense row-major B (num_cols rows of K values, row pitch ldb):
+ * for every row i and column j of B, C[i][j] = sum over k in [rp[i], rp[i+1])
+ * of v[k] * B[ci[k]][j] -- the SpMV loop of Listing 3 inside a loop over the
+ * columns of B, as Sec. 7 (Listing 4) extends it; B is read at the atom's
+ * column index.  FP64 in atom order; bnd[i][j] = sum |v[k] B[ci[k]][j]| for the
+ * acceptance bound.  C and bnd are row-major R x K.  Empty rows give 0.
+ */
+void or_spmm(int32_t R, const int32_t* rp, const int32_t* ci, const float* v, const float* B, int64_t ldb,
+             int32_t K, double* C, double* bnd) {
+  for (int32_t i = 0; i < R; ++i) {
+    for (int32_t j = 0; j < K; ++j) {
+      double s = 0.0, a = 0.0;
+      for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+        double p = (double)v[k] * (double)B[(int64_t)ci[k] * ldb + j];
+        s += p;
+        a += fabs(p);
+      }
+      C[(int64_t)i * K + j] = s;
+      if (bnd) bnd[(int64_t)i * K + j] = a;
+    }
+  }
+}
+
+/*
  * Same as or_spmv for a subset of rows (sampled parity at full size).
  */
 void or_spmv_rows(int64_t nsel, const int64_t* rows, const int32_t* rp, const int32_t* ci, const float* v,

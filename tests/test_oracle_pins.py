@@ -263,6 +263,44 @@ def test_fd_instance_500x500():
         assert abs(dx[c] - fd) <= 1e-9 * max(1.0, abs(fd))
 
 
+def check_spmm(orc):
+    """SpMM (Listing 4) against dense brute force, the identity and SpMV column by column."""
+    rng = np.random.default_rng(11)
+    for R, C, K in ((0, 3, 4), (1, 1, 1), (7, 5, 3), (40, 33, 32), (33, 40, 33), (20, 20, 64)):
+        dens = rng.uniform(0.0, 0.6)
+        mask = rng.random((R, C)) < dens
+        if R > 2:
+            mask[1, :] = False          # an empty row
+            mask[2, :] = True           # a full row
+        rp = np.concatenate([[0], np.cumsum(mask.sum(1))]).astype(np.int32)
+        ci = np.nonzero(mask)[1].astype(np.int32)
+        v = rng.uniform(-1, 1, ci.shape[0]).astype(np.float32)
+        B = rng.uniform(-1, 1, (C, K)).astype(np.float32)
+        out, b = orc.spmm(rp, ci, v, B)
+        A = dense_of(rp, ci, v, C)
+        ref = A @ B.astype(np.float64)
+        assert out.shape == (R, K)
+        assert (np.abs(out - ref) <= 1e-12 * (np.abs(A) @ np.abs(B.astype(np.float64))) + 1e-300).all()
+        assert np.allclose(b, np.abs(A) @ np.abs(B.astype(np.float64)), rtol=1e-12, atol=0)
+        # one column of B at a time is SpMV
+        for j in (0, K - 1):
+            y, _ = orc.spmv(rp, ci, v, B[:, j].copy())
+            assert np.array_equal(out[:, j], y)
+    # identity: C = B exactly; a row permutation permutes B's rows
+    n, K = 50, 17
+    B = rng.uniform(-1, 1, (n, K)).astype(np.float32)
+    rp = np.arange(n + 1, dtype=np.int32)
+    out, _ = orc.spmm(rp, np.arange(n, dtype=np.int32), np.ones(n, np.float32), B)
+    assert np.array_equal(out, B.astype(np.float64))
+    perm = rng.permutation(n).astype(np.int32)
+    out, _ = orc.spmm(rp, perm, np.ones(n, np.float32), B)
+    assert np.array_equal(out, B[perm].astype(np.float64))
+
+
+def test_spmm_against_dense_identity_and_spmv():
+    check_spmm(oracle.default())
+
+
 # ------------------------------------------------------------ mutation tests --
 
 MUTANTS = {
@@ -284,6 +322,9 @@ MUTANTS = {
                             "dvals[k] = (float)((double)dy[r] * (double)x[r % C]);", check_grad),
     # sign error in dx
     "dx_sign": ("dx[ci[k]] += p;", "dx[ci[k]] -= p;", check_grad),
+    # wrong column of B in SpMM: the columns of B read in reverse order
+    "spmm_wrong_b_column": ("(double)B[(int64_t)ci[k] * ldb + j];", "(double)B[(int64_t)ci[k] * ldb + (K - 1 - j)];",
+                            check_spmm),
 }
 
 
