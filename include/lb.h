@@ -313,6 +313,29 @@ lb_status_t lb_autotune(const int32_t* tile_offsets, int32_t num_tiles, int32_t 
                         lb_tune_result_t* result, lb_plan_t* out_plan, void* stream);
 /* Empties the autotuner's process-wide cache. */
 void lb_autotune_cache_clear(void);
+/* ------------------------------------------------------------------ SpMM -- */
+/*
+ * C = A B for a dense row-major B (Sec. 7, Listing 4: the SpMV loop with one
+ * more loop over the columns of B): C[t][j] = sum over atoms k of tile t of
+ * vals[k] * B[col_idx[k]][j].  B: float, num_cols rows of K values at row
+ * pitch ldb >= K; C: float, num_tiles rows of K values at pitch ldc >= K,
+ * overwritten.  Schedules: merge-path plans (a warp per share of rows + atoms,
+ * the lanes holding B's columns; rows split between shares are finished by a
+ * second launch that adds each run of partial sums in order) and thread-mapped
+ * plans (Listing 4 as printed: a thread per row looping over the columns and
+ * the row's atoms); other schedules and batch plans give LB_ERR_UNSUPPORTED.
+ * Columns go in panels of 128.  Sums are chunked (at most one warp tile or
+ * 256 atoms before a partial is added to the row's running sum) and in a fixed
+ * order, so results are bit-identical run to run.  No allocation or sync once
+ * lb_prepare_spmm has run (lb_spmm calls it first otherwise).
+ * Errors: LB_ERR_INVALID_ARG (K < 0, ldb or ldc < K, NULL buffers),
+ * LB_ERR_UNSUPPORTED, LB_ERR_OOM, LB_ERR_CUDA.
+ */
+lb_status_t lb_spmm(lb_plan_t plan, int32_t K, const int32_t* col_idx, const float* vals, const float* B, int64_t ldb,
+                    float* C, int64_t ldc, void* stream);
+/* Builds the SpMM table and carry slots of a merge-path plan (allocates, synchronises `stream`);
+ * nothing to do for a thread-mapped plan. */
+lb_status_t lb_prepare_spmm(lb_plan_t plan, void* stream);
 /* -------------------------------------------------------------- batching -- */
 
 /*

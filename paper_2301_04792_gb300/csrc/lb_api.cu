@@ -267,6 +267,9 @@ lb_status_t lb_plan(lb_plan_t* out, const int32_t* tile_offsets, int32_t num_til
 void lb_plan_destroy(lb_plan_t p) {
   if (!p) return;
   p->mp.release();
+  p->mm.release();
+  cudaFree(p->mm_carry_row);
+  cudaFree(p->mm_carry_val);
   free_transpose(p);
   p->bb.release();
   cudaFree(p->rp_global);

@@ -108,6 +108,11 @@ struct lb_plan_s {
   int32_t* riT = nullptr;
   int32_t* perm = nullptr;
   lbh::MpTable mp_t;
+  // SpMM (merge-path plans): warp-tile table, carries of a column panel
+  bool mm_ready = false;
+  lbh::MpTable mm;
+  int32_t* mm_carry_row = nullptr;
+  float* mm_carry_val = nullptr;
   // batch
   int32_t* rp_global = nullptr;  // owned global row offsets
   lbh::BatchBases bb;

@@ -171,6 +171,25 @@ class Plan:
                                 ctypes.c_void_p(_stream(stream))), "lb_spmv")
         return y
 
+    def spmm(self, col_idx: torch.Tensor, vals: torch.Tensor, B: torch.Tensor, C: torch.Tensor | None = None,
+             stream=None) -> torch.Tensor:
+        """C = A B (``lb_spmm``) for a dense B [num_cols, K] whose rows are contiguous
+        (row stride >= K, unit column stride); C [num_tiles, K] likewise."""
+        _need(col_idx, torch.int32, "col_idx", self.num_atoms)
+        _need(vals, torch.float32, "vals", self.num_atoms)
+        if not isinstance(B, torch.Tensor) or B.dim() != 2 or not B.is_cuda or B.dtype != torch.float32:
+            raise TypeError("B must be a 2-D float32 CUDA tensor")
+        if B.stride(1) != 1 or B.stride(0) < B.shape[1]:
+            raise ValueError("B must have unit column stride and row stride >= its width")
+        K = B.shape[1]
+        if C is None:
+            C = torch.empty(self.num_tiles, K, dtype=torch.float32, device=B.device)
+        if C.dim() != 2 or C.shape != (self.num_tiles, K) or C.stride(1) != 1 or C.dtype != torch.float32:
+            raise ValueError("C must be float32 [num_tiles, K] with unit column stride")
+        check(self._lib.lb_spmm(self.handle, int(K), _ptr(col_idx), _ptr(vals), _ptr(B), int(B.stride(0)), _ptr(C),
+                                int(C.stride(0)), ctypes.c_void_p(_stream(stream))), "lb_spmm")
+        return C
+
     def prepare_backward(self, num_cols: int, col_idx: torch.Tensor, stream=None):
         _need(col_idx, torch.int32, "col_idx", self.num_atoms)
         check(self._lib.lb_prepare_backward(self.handle, int(num_cols), _ptr(col_idx),
