@@ -587,6 +587,31 @@ def run_ours(args, ws, rank, local):
     e2e_ok = bool(np.allclose(h_y.numpy()[sample].astype(np.float64), y64, atol=0, rtol=0) or
                   (np.abs(h_y.numpy()[sample].astype(np.float64) - y64) <= oracle.TOL * bnd).all())
 
+    # SpMM C = A B (Listing 4) on the same matrix, B dense [cols, K]
+    spmm = None
+    if not args.quick and not args.ncu:
+        spmm = {}
+        rng = np.random.default_rng(5)
+        for K in (8, 32, 128):
+            Bh = rng.uniform(-1, 1, (C, K)).astype(np.float32)
+            Bd = torch.from_numpy(Bh).to(device)
+            Cd = torch.empty(R, K, device=device)
+            p = lb.Plan(rp_d[0], N, "merge_path", num_cols=C)
+            p.spmm(ci_d[0], v_d[0], Bd, Cd)
+            durs = time_launches(torch, lambda i: p.spmm(ci_d[i % copies], v_d[i % copies], Bd, Cd), 20, stream)
+            ms = statistics.median(durs)
+            c64, cb = oracle.spmm(m.rp[: 2001], m.ci, m.v, Bh)  # parity on the first 2000 rows
+            ok = bool((np.abs(Cd[:2000].cpu().numpy().astype(np.float64) - c64) <= oracle.TOL * cb).all())
+            mm_bytes = 8 * N + 4 * (R + 1) + 4 * C * K + 4 * R * K
+            # every atom reads one K-wide row of B: once B outgrows L2 that is the traffic
+            gather_bytes = 8 * N + 4 * (R + 1) + 4 * N * K + 4 * R * K
+            spmm[f"K{K}"] = {"ms": round(ms, 4), "GBps": round(mm_bytes / (ms * 1e-3) / 1e9, 2),
+                             "GFLOPs": round(2 * N * K / (ms * 1e-3) / 1e9, 2), "parity_first_2000_rows": ok,
+                             "algorithmic_bytes": mm_bytes, "B_MB": round(4 * C * K / 1e6, 1),
+                             "row_gather_GBps": round(gather_bytes / (ms * 1e-3) / 1e9, 2)}
+            p.close()
+            del Bd, Cd
+
     batched = None
     if not args.no_batch and not args.ncu:
         batched = bench_batched(torch, lb, W, device)
@@ -617,6 +642,7 @@ def run_ours(args, ws, rank, local):
             "parity_sampled_rows_ok": parity_ok,
             "roofline": roofline,
             "autotune": tune,
+            "spmm_merge_path": spmm,
             "schedules_GBps": sched,
             "e2e": {"value": round(e2e_val, 2), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": round(e2e_ms, 4), "ok": e2e_ok},

@@ -43,14 +43,26 @@ struct SpmmArgs {
 template <int KB>
 __global__ void __launch_bounds__(256) spmm_mp_kernel(SpmmArgs a) {
   constexpr int WPB = 8;
+  constexpr int U = KB == 1 ? 16 : 8;  // rows of B in flight per lane
   __shared__ int s_ci[WPB][kTileCap];
   __shared__ float s_v[WPB][kTileCap];
-  __shared__ int s_end[WPB][kTileCap];
+  __shared__ int s_mark[WPB][kTileCap];   // row (local) that ends at this atom, -1 if none
+  __shared__ int s_empty[WPB][kTileCap];  // rows (local, > 0) with no atoms in the tile
+  __shared__ int s_nempty[WPB];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int* ci_s = s_ci[warp];
   float* v_s = s_v[warp];
-  int* end_s = s_end[warp];
+  int* mark_s = s_mark[warp];
+  int* empty_s = s_empty[warp];
   const int nwarps = gridDim.x * WPB;
+  auto store_row = [&](int row, const float (&val)[KB]) {
+    float* crow = a.C + (int64_t)row * a.ldc;
+#pragma unroll
+    for (int kb = 0; kb < KB; ++kb) {
+      const int col = lane + 32 * kb;
+      if (col < a.K) crow[col] = val[kb];
+    }
+  };
   for (int s = blockIdx.x * WPB + warp; s < a.num_shares; s += nwarps) {
     const int2* sp = a.splits + (size_t)s * (a.tpc + 1);
     int2 c0 = __ldg(sp);
@@ -62,63 +74,89 @@ __global__ void __launch_bounds__(256) spmm_mp_kernel(SpmmArgs a) {
     for (int k = 0; k < ntiles; ++k) {
       const int2 c1 = __ldg(sp + k + 1);
       const int nnz = c1.y - c0.y, nrows = c1.x - c0.x;
+      // stage the tile's atoms; mark the atom each closing row ends at
       for (int i = lane; i < nnz; i += 32) {
         ci_s[i] = lbk::ld_stream(a.idx + c0.y + i);
         v_s[i] = lbk::ld_stream(a.val + c0.y + i);
+        mark_s[i] = -1;
       }
-      for (int i = lane; i < nrows; i += 32) end_s[i] = __ldg(a.rp + c0.x + 1 + i) - c0.y;
+      if (lane == 0) s_nempty[warp] = 0;
       __syncwarp();
-      int j = 0;
-      // rows closing in the tile, then the row left open at its end (r == nrows)
-      for (int r = 0; r <= nrows; ++r) {
-        const int e = r < nrows ? end_s[r] : nnz;
-        float p[KB];
+      bool first_empty = false;  // row 0 closes at the tile's start with no atoms here
+      for (int rb = 0; rb < nrows; rb += 32) {
+        const int r = rb + lane;
+        int e = 0, pe = 0;
+        if (r < nrows) {
+          e = __ldg(a.rp + c0.x + 1 + r) - c0.y;
+          pe = r == 0 ? 0 : __ldg(a.rp + c0.x + r) - c0.y;
+        }
+        const bool has = r < nrows && e > pe;
+        if (has) mark_s[e - 1] = r;
+        const bool empty = r < nrows && !has;
+        if (empty && r == 0) first_empty = true;
+        const unsigned em = __ballot_sync(lbk::kFull, empty && r > 0);
+        if (empty && r > 0) empty_s[s_nempty[warp] + __popc(em & ((1u << lane) - 1u))] = r;
+        __syncwarp();
+        if (lane == 0) s_nempty[warp] += __popc(em);
+        __syncwarp();
+      }
+      first_empty = __any_sync(lbk::kFull, first_empty);
+      if (first_empty) {  // its value is the earlier tiles' partial sum
+        store_row(c0.x, carry);
 #pragma unroll
-        for (int kb = 0; kb < KB; ++kb) p[kb] = 0.f;
-        int q = j;
-        for (; q + 4 <= e; q += 4) {
-          float bq[4][KB];
+        for (int kb = 0; kb < KB; ++kb) carry[kb] = 0.f;
+      }
+      {
+        float zero[KB];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float* brow = a.B + (int64_t)ci_s[q + u] * a.ldb;
+        for (int kb = 0; kb < KB; ++kb) zero[kb] = 0.f;
+        const int ne = s_nempty[warp];
+        for (int q = 0; q < ne; ++q) store_row(c0.x + empty_s[q], zero);
+      }
+      // the atoms in order, U rows of B in flight; a marked atom closes its row
+      // (row 0 gets the earlier tiles' partial sum in front of its own)
+      float p[KB];
 #pragma unroll
-            for (int kb = 0; kb < KB; ++kb) {
-              const int col = lane + 32 * kb;
-              bq[u][kb] = col < a.K ? __ldg(brow + col) : 0.f;
-            }
+      for (int kb = 0; kb < KB; ++kb) p[kb] = 0.f;
+      for (int q0 = 0; q0 < nnz; q0 += U) {
+        float bq[U][KB];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int q = q0 + u;
+          const float* brow = a.B + (int64_t)(q < nnz ? ci_s[q] : 0) * a.ldb;
+#pragma unroll
+          for (int kb = 0; kb < KB; ++kb) {
+            const int col = lane + 32 * kb;
+            bq[u][kb] = (q < nnz && col < a.K) ? __ldg(brow + col) : 0.f;
           }
+        }
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float w = v_s[q + u];
+        for (int u = 0; u < U; ++u) {
+          const int q = q0 + u;
+          if (q < nnz) {
+            const float w = v_s[q];
 #pragma unroll
             for (int kb = 0; kb < KB; ++kb) p[kb] += w * bq[u][kb];
+            const int r = mark_s[q];
+            if (r >= 0) {
+              if (r == 0) {
+#pragma unroll
+                for (int kb = 0; kb < KB; ++kb) p[kb] = carry[kb] + p[kb];
+              }
+              store_row(c0.x + r, p);
+#pragma unroll
+              for (int kb = 0; kb < KB; ++kb) p[kb] = 0.f;
+            }
           }
         }
-        for (; q < e; ++q) {
-          const float* brow = a.B + (int64_t)ci_s[q] * a.ldb;
-          const float w = v_s[q];
+      }
+      // the row open at the tile's end: its partial joins the running sum
+      if (nrows == 0) {
 #pragma unroll
-          for (int kb = 0; kb < KB; ++kb) {
-            const int col = lane + 32 * kb;
-            p[kb] += w * (col < a.K ? __ldg(brow + col) : 0.f);
-          }
-        }
-        if (r == 0) {  // the row open at the tile's start: the earlier tiles' partial sum in front
+        for (int kb = 0; kb < KB; ++kb) carry[kb] = carry[kb] + p[kb];
+      } else {
 #pragma unroll
-          for (int kb = 0; kb < KB; ++kb) p[kb] = carry[kb] + p[kb];
-        }
-        if (r < nrows) {
-          float* crow = a.C + (int64_t)(c0.x + r) * a.ldc;
-#pragma unroll
-          for (int kb = 0; kb < KB; ++kb) {
-            const int col = lane + 32 * kb;
-            if (col < a.K) crow[col] = p[kb];
-          }
-        } else {
-#pragma unroll
-          for (int kb = 0; kb < KB; ++kb) carry[kb] = p[kb];
-        }
-        j = e;
+        for (int kb = 0; kb < KB; ++kb) carry[kb] = p[kb];
       }
       __syncwarp();
       c0 = c1;
@@ -130,6 +168,92 @@ __global__ void __launch_bounds__(256) spmm_mp_kernel(SpmmArgs a) {
       const int col = lane + 32 * kb;
       if (col < a.K) a.carry_val[(size_t)s * kPanel + col] = carry[kb];
     }
+  }
+}
+
+// The same walk with 16-byte rows of B: lane l holds columns 4 (l mod CL) ..
+// 4 (l mod CL) + 3 of the panel, so a row of B is CL float4 loads and the warp
+// takes G = 32 / CL atoms per instruction (group l / CL takes every G-th atom
+// of a row, four rounds in flight); at the row's end a fixed butterfly over
+// the groups adds their sums, leaving the same total in every group.  Needs
+// B, C 16-byte aligned, ldb, ldc and the panel width multiples of 4.
+template <int CL>
+__global__ void __launch_bounds__(256) spmm_mp_vec_kernel(SpmmArgs a) {
+  constexpr int WPB = 8;
+  constexpr int G = 32 / CL;
+  constexpr int U = 4;
+  __shared__ int2 s_cv[WPB][kTileCap];
+  __shared__ int s_end[WPB][kTileCap];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane / CL, col = 4 * (lane % CL);
+  const bool active = col < a.K;
+  int2* cv_s = s_cv[warp];
+  int* end_s = s_end[warp];
+  const int nwarps = gridDim.x * WPB;
+  for (int s = blockIdx.x * WPB + warp; s < a.num_shares; s += nwarps) {
+    const int2* sp = a.splits + (size_t)s * (a.tpc + 1);
+    int2 c0 = __ldg(sp);
+    const int2 e1 = __ldg(sp + a.tpc);
+    const int ntiles = (int)(((int64_t)(e1.x - c0.x) + (e1.y - c0.y) + a.items_per_tile - 1) / a.items_per_tile);
+    float4 carry = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = 0; k < ntiles; ++k) {
+      const int2 c1 = __ldg(sp + k + 1);
+      const int nnz = c1.y - c0.y, nrows = c1.x - c0.x;
+      for (int i = lane; i < nnz; i += 32)
+        cv_s[i] = make_int2(lbk::ld_stream(a.idx + c0.y + i), __float_as_int(lbk::ld_stream(a.val + c0.y + i)));
+      for (int i = lane; i < nrows; i += 32) end_s[i] = __ldg(a.rp + c0.x + 1 + i) - c0.y;
+      __syncwarp();
+      int j = 0;
+      for (int r = 0; r <= nrows; ++r) {
+        const int e = r < nrows ? end_s[r] : nnz;
+        float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int q0 = j; q0 < e; q0 += U * G) {
+          float4 bq[U];
+          float w[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int q = q0 + u * G + g;
+            w[u] = 0.f;
+            bq[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (q < e) {
+              const int2 cv = cv_s[q];
+              w[u] = __int_as_float(cv.y);
+              if (active) bq[u] = __ldg(reinterpret_cast<const float4*>(a.B + (int64_t)cv.x * a.ldb + col));
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            p.x += w[u] * bq[u].x;
+            p.y += w[u] * bq[u].y;
+            p.z += w[u] * bq[u].z;
+            p.w += w[u] * bq[u].w;
+          }
+        }
+#pragma unroll
+        for (int o = CL; o < 32; o <<= 1) {
+          p.x += __shfl_xor_sync(lbk::kFull, p.x, o);
+          p.y += __shfl_xor_sync(lbk::kFull, p.y, o);
+          p.z += __shfl_xor_sync(lbk::kFull, p.z, o);
+          p.w += __shfl_xor_sync(lbk::kFull, p.w, o);
+        }
+        if (r == 0) {  // the row open at the tile's start: the earlier tiles' partial sum in front
+          p.x = carry.x + p.x;
+          p.y = carry.y + p.y;
+          p.z = carry.z + p.z;
+          p.w = carry.w + p.w;
+        }
+        if (r < nrows) {
+          if (g == 0 && active) *reinterpret_cast<float4*>(a.C + (int64_t)(c0.x + r) * a.ldc + col) = p;
+        } else {
+          carry = p;
+        }
+        j = e;
+      }
+      __syncwarp();
+      c0 = c1;
+    }
+    if (lane == 0) a.carry_row[s] = c0.x < a.R ? c0.x : -1;
+    if (g == 0 && active) *reinterpret_cast<float4*>(a.carry_val + (size_t)s * kPanel + col) = carry;
   }
 }
 
@@ -184,18 +308,43 @@ __global__ void __launch_bounds__(256) spmm_tm_kernel(const int32_t* __restrict_
   }
 }
 
+template <int KB>
 int spmm_grid(int sms) {
-  static int occ = 0;
+  static int occ = 0;  // per instantiation
   if (occ == 0) {
     int o = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, spmm_mp_kernel<4>, kBlock, 0) != cudaSuccess || o < 1) o = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, spmm_mp_kernel<KB>, kBlock, 0) != cudaSuccess || o < 1) o = 1;
     occ = o;
   }
   return sms * occ;
 }
 
+template <int CL>
+int spmm_vec_grid(int sms) {
+  static int occ = 0;  // per instantiation
+  if (occ == 0) {
+    int o = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, spmm_mp_vec_kernel<CL>, kBlock, 0) != cudaSuccess || o < 1)
+      o = 1;
+    occ = o;
+  }
+  return sms * occ;
+}
+
+template <int CL>
+cudaError_t launch_vec_panel(const SpmmArgs& a, int sms, cudaStream_t s) {
+  const int grid = std::max(1, std::min(spmm_vec_grid<CL>(sms), (a.num_shares + 7) / 8));
+  spmm_mp_vec_kernel<CL><<<grid, kBlock, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // the fix-up reads the carries column by column (its layout is the same)
+  spmm_fixup_kernel<CL <= 8 ? 1 : CL / 8><<<grid, kBlock, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <int KB>
-cudaError_t launch_panel(const SpmmArgs& a, int grid, cudaStream_t s) {
+cudaError_t launch_panel(const SpmmArgs& a, int sms, cudaStream_t s) {
+  const int grid = std::max(1, std::min(spmm_grid<KB>(sms), (a.num_shares + 7) / 8));
   spmm_mp_kernel<KB><<<grid, kBlock, 0, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -266,7 +415,6 @@ lb_status_t lb_spmm(lb_plan_t p, int32_t K, const int32_t* col_idx, const float*
     return LB_OK;
   }
   LB_TRY(lb_prepare_spmm(p, stream));
-  const int grid = spmm_grid(p->num_sms);
   for (int col0 = 0; col0 < K; col0 += kPanel) {
     SpmmArgs a{};
     a.rp = p->rp;
@@ -284,8 +432,21 @@ lb_status_t lb_spmm(lb_plan_t p, int32_t K, const int32_t* col_idx, const float*
     a.items_per_tile = p->mm.items_per_tile;
     a.carry_row = p->mm_carry_row;
     a.carry_val = p->mm_carry_val;
-    const int g = std::max(1, std::min(grid, (a.num_shares + 7) / 8));
-    cudaError_t e = a.K <= 32 ? launch_panel<1>(a, g, s) : a.K <= 64 ? launch_panel<2>(a, g, s) : launch_panel<4>(a, g, s);
+    const bool vec = ((reinterpret_cast<uintptr_t>(a.B) | reinterpret_cast<uintptr_t>(a.C)) & 15u) == 0 &&
+                     (ldb & 3) == 0 && (ldc & 3) == 0 && (a.K & 3) == 0;
+    cudaError_t e;
+    if (vec) {
+      const int cl = (a.K + 3) / 4;  // float4 lanes per row of the panel
+      e = cl <= 2    ? launch_vec_panel<2>(a, p->num_sms, s)
+          : cl <= 4  ? launch_vec_panel<4>(a, p->num_sms, s)
+          : cl <= 8  ? launch_vec_panel<8>(a, p->num_sms, s)
+          : cl <= 16 ? launch_vec_panel<16>(a, p->num_sms, s)
+                     : launch_vec_panel<32>(a, p->num_sms, s);
+    } else {
+      e = a.K <= 32   ? launch_panel<1>(a, p->num_sms, s)
+          : a.K <= 64 ? launch_panel<2>(a, p->num_sms, s)
+                      : launch_panel<4>(a, p->num_sms, s);
+    }
     LB_CUDA_TRY(e);
   }
   return LB_OK;

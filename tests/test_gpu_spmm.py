@@ -48,7 +48,7 @@ def check(lb, m, K, schedule, seed=0, pad_b=0, pad_c=0, reps=2, **kw):
         assert torch.equal(c2.view(torch.int32), outs[0][0].view(torch.int32)), "SpMM not bit-identical"
 
 
-@pytest.mark.parametrize("K", [1, 7, 32, 33, 64, 100, 128, 130])
+@pytest.mark.parametrize("K", [1, 7, 8, 16, 32, 33, 64, 100, 128, 130, 256])
 def test_spmm_small_cases(lbmod, K):
     for name, m in small_cases() + edge_cases():
         check(lbmod, m, K, "merge_path")
@@ -59,7 +59,9 @@ def test_spmm_small_cases(lbmod, K):
 def test_spmm_pitched_and_long_rows(lbmod):
     m = W.from_lengths(np.array([30_000, 3, 0, 0, 45_000, 1, 900, 0]), 50_000, seed=12)
     for K in (16, 96, 257):
-        check(lbmod, m, K, "merge_path", pad_b=5, pad_c=3, reps=3)
+        check(lbmod, m, K, "merge_path", pad_b=5, pad_c=3, reps=3)   # scalar path (pitch not a multiple of 4)
+    for K in (8, 32, 124):
+        check(lbmod, m, K, "merge_path", pad_b=4, pad_c=8, reps=3)   # 16-byte rows of B and C
     check(lbmod, W.plain(300, 300, 3, seed=2), 40, "thread_mapped", pad_b=2, pad_c=1)
 
 
