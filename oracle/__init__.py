@@ -56,6 +56,8 @@ def _bind(lib):
     f64p = ctypes.POINTER(ctypes.c_double)
     lib.or_spmv.argtypes = [ctypes.c_int32, i32p, i32p, f32p, f32p, f64p, f64p]
     lib.or_spmv_rows.argtypes = [ctypes.c_int64, i64p, i32p, i32p, f32p, f32p, f64p, f64p]
+    lib.or_sssp.argtypes = [ctypes.c_int32, i32p, i32p, f32p, ctypes.c_int32, f32p]
+    lib.or_sssp.restype = ctypes.c_int32
     lib.or_spmm.argtypes = [ctypes.c_int32, i32p, i32p, f32p, f32p, ctypes.c_int64, ctypes.c_int32, f64p, f64p]
     lib.or_merge_split.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, i32p]
     lib.or_merge_split.restype = ctypes.c_int32
@@ -109,6 +111,16 @@ class Oracle:
         self.lib.or_spmm(R, _p(rp, ctypes.c_int32), _p(ci, ctypes.c_int32), _p(v, ctypes.c_float),
                          _p(B, ctypes.c_float), K, K, _p(C, ctypes.c_double), _p(b, ctypes.c_double))
         return C, b
+
+    def sssp(self, rp, ci, w, source: int):
+        """float32 [V] shortest distances from `source` (+inf if unreachable), Listing 5's float
+        arithmetic, by Dijkstra's algorithm."""
+        rp, ci, w = _c(rp, np.int32), _c(ci, np.int32), _c(w, np.float32)
+        V = rp.shape[0] - 1
+        dist = np.empty(V, dtype=np.float32)
+        self.lib.or_sssp(V, _p(rp, ctypes.c_int32), _p(ci, ctypes.c_int32), _p(w, ctypes.c_float), int(source),
+                         _p(dist, ctypes.c_float))
+        return dist
 
     def spmv_threads(self, rp, ci, v, x, threads: int):
         """(y64, b) as spmv, the rows cut into `threads` blocks of about equal rows + atoms,
@@ -237,6 +249,10 @@ def spmv_threads(rp, ci, v, x, threads: int):
 
 def spmm(rp, ci, v, B):
     return default().spmm(rp, ci, v, B)
+
+
+def sssp(rp, ci, w, source: int):
+    return default().sssp(rp, ci, w, source)
 
 
 def merge_split(d, rp):

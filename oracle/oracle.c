@@ -211,3 +211,74 @@ void or_grad(int32_t R, int32_t C, const int32_t* rp, const int32_t* ci, const f
     }
   }
 }
+
+/*
+ * Single-source shortest paths (Sec. 7, Listing 5) with the listing's float
+ * distances: dist[source] = 0 and, for every other vertex v reachable from the
+ * source, dist[v] = min over edges (u, v) of fl32(dist[u] + w(u, v)); +inf if
+ * unreachable.  Vertices are tiles, their out-edges atoms (CSR rp / ci, edge
+ * weights w >= 0).  Dijkstra's algorithm: settle vertices in order of
+ * distance from a binary min-heap (entries pushed on every improvement, stale
+ * ones skipped when popped).  Returns the number of vertices settled.
+ */
+typedef struct {
+  float d;
+  int32_t v;
+} or_heap_item;
+
+static void or_heap_push(or_heap_item* h, int64_t* n, float d, int32_t v) {
+  int64_t i = (*n)++;
+  while (i > 0) {
+    int64_t p = (i - 1) / 2;
+    if (h[p].d <= d) break;
+    h[i] = h[p];
+    i = p;
+  }
+  h[i].d = d;
+  h[i].v = v;
+}
+
+static or_heap_item or_heap_pop(or_heap_item* h, int64_t* n) {
+  or_heap_item top = h[0];
+  or_heap_item last = h[--(*n)];
+  int64_t i = 0;
+  for (;;) {
+    int64_t c = 2 * i + 1;
+    if (c >= *n) break;
+    if (c + 1 < *n && h[c + 1].d < h[c].d) ++c;
+    if (last.d <= h[c].d) break;
+    h[i] = h[c];
+    i = c;
+  }
+  if (*n > 0) h[i] = last;
+  return top;
+}
+
+int32_t or_sssp(int32_t V, const int32_t* rp, const int32_t* ci, const float* w, int32_t src, float* dist) {
+  for (int32_t v = 0; v < V; ++v) dist[v] = INFINITY;
+  if (V == 0) return 0;
+  int64_t cap = (int64_t)rp[V] + 1;
+  or_heap_item* h = (or_heap_item*)malloc(sizeof(or_heap_item) * (size_t)cap);
+  unsigned char* done = (unsigned char*)calloc((size_t)V, 1);
+  int64_t n = 0;
+  int32_t settled = 0;
+  dist[src] = 0.0f;
+  or_heap_push(h, &n, 0.0f, src);
+  while (n > 0) {
+    or_heap_item it = or_heap_pop(h, &n);
+    if (done[it.v] || it.d > dist[it.v]) continue;
+    done[it.v] = 1;
+    ++settled;
+    for (int32_t k = rp[it.v]; k < rp[it.v + 1]; ++k) {
+      int32_t u = ci[k];
+      float nd = dist[it.v] + w[k];
+      if (nd < dist[u]) {
+        dist[u] = nd;
+        or_heap_push(h, &n, nd, u);
+      }
+    }
+  }
+  free(h);
+  free(done);
+  return settled;
+}

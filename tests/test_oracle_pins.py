@@ -301,6 +301,80 @@ def test_spmm_against_dense_identity_and_spmv():
     check_spmm(oracle.default())
 
 
+def bellman_ford32(rp, ci, w, src):
+    """Plain Bellman-Ford in float32: relax every edge, in edge order, until nothing changes."""
+    V = len(rp) - 1
+    d = np.full(V, np.inf, dtype=np.float32)
+    if V == 0:
+        return d
+    d[src] = np.float32(0)
+    row = np.repeat(np.arange(V), np.diff(rp))
+    for _ in range(V + 1):
+        changed = False
+        for k in range(len(ci)):
+            nd = np.float32(d[row[k]] + w[k])
+            if nd < d[ci[k]]:
+                d[ci[k]] = nd
+                changed = True
+        if not changed:
+            break
+    return d
+
+
+def random_graph(rng, V, E, wmax=1.0, zero_frac=0.0):
+    src = rng.integers(0, V, E)
+    dst = rng.integers(0, V, E)
+    order = np.lexsort((dst, src))
+    src, dst = src[order], dst[order]
+    rp = np.concatenate([[0], np.cumsum(np.bincount(src, minlength=V))]).astype(np.int32)
+    w = rng.uniform(0, wmax, E).astype(np.float32)
+    w[rng.random(E) < zero_frac] = 0.0
+    return rp, dst.astype(np.int32), w
+
+
+def check_sssp(orc):
+    """SSSP (Listing 5, float distances) against Bellman-Ford in float32 (bit-exact), BFS levels for
+    unit weights, and scipy's FP64 Dijkstra within the float rounding of the path sums."""
+    rng = np.random.default_rng(21)
+    cases = [(1, 0, 0.0), (2, 1, 0.0), (6, 10, 0.0), (30, 90, 0.0), (50, 60, 0.0), (40, 200, 0.3), (64, 400, 0.0)]
+    for V, E, zf in cases:
+        rp, ci, w = random_graph(rng, V, E, zero_frac=zf)
+        for s in sorted({0, V - 1}):
+            d = orc.sssp(rp, ci, w, s)
+            ref = bellman_ford32(rp, ci, w, s)
+            assert np.array_equal(d.view(np.int32), ref.view(np.int32)), (V, E, s)
+    # unit weights: breadth-first levels
+    rp, ci, _ = random_graph(rng, 80, 240)
+    d = orc.sssp(rp, ci, np.ones(len(ci), np.float32), 3)
+    lev = np.full(80, np.inf)
+    lev[3] = 0
+    front = [3]
+    while front:
+        nxt = []
+        for u in front:
+            for k in range(rp[u], rp[u + 1]):
+                if lev[ci[k]] == np.inf:
+                    lev[ci[k]] = lev[u] + 1
+                    nxt.append(ci[k])
+        front = nxt
+    assert np.array_equal(d.astype(np.float64), lev)
+    # FP64 Dijkstra of a library: the same reachable set, distances within path-sum rounding
+    sp = pytest.importorskip("scipy.sparse")
+    csg = pytest.importorskip("scipy.sparse.csgraph")
+    rp, ci, w = random_graph(rng, 500, 3000)
+    w = w + np.float32(0.01)
+    d = orc.sssp(rp, ci, w, 0)
+    A = sp.csr_matrix((w.astype(np.float64), ci, rp), shape=(500, 500))
+    d64 = csg.dijkstra(A, directed=True, indices=0)
+    assert np.array_equal(np.isinf(d), np.isinf(d64))
+    fin = np.isfinite(d64)
+    assert (np.abs(d[fin] - d64[fin]) <= 1e-5 * d64[fin] + 1e-30).all()
+
+
+def test_sssp_against_bellman_ford_bfs_and_fp64_dijkstra():
+    check_sssp(oracle.default())
+
+
 # ------------------------------------------------------------ mutation tests --
 
 MUTANTS = {
@@ -322,6 +396,8 @@ MUTANTS = {
                             "dvals[k] = (float)((double)dy[r] * (double)x[r % C]);", check_grad),
     # sign error in dx
     "dx_sign": ("dx[ci[k]] += p;", "dx[ci[k]] -= p;", check_grad),
+    # SSSP relaxing with a dropped weight (distance of the source carried unchanged)
+    "sssp_dropped_weight": ("float nd = dist[it.v] + w[k];", "float nd = dist[it.v] + 0.0f * w[k];", check_sssp),
     # wrong column of B in SpMM: the columns of B read in reverse order
     "spmm_wrong_b_column": ("(double)B[(int64_t)ci[k] * ldb + j];", "(double)B[(int64_t)ci[k] * ldb + (K - 1 - j)];",
                             check_spmm),
