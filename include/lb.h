@@ -336,6 +336,25 @@ lb_status_t lb_spmm(lb_plan_t plan, int32_t K, const int32_t* col_idx, const flo
 /* Builds the SpMM table and carry slots of a merge-path plan (allocates, synchronises `stream`);
  * nothing to do for a thread-mapped plan. */
 lb_status_t lb_prepare_spmm(lb_plan_t plan, void* stream);
+/* ------------------------------------------------------------------ SSSP -- */
+/*
+ * Single-source shortest paths (Sec. 7, Listing 5) on the group-mapped
+ * schedule.  The graph is a CSR tile set: vertex v's out-edges are the atoms
+ * [tile_offsets[v], tile_offsets[v+1]) with heads col_idx[k] in
+ * [0, num_vertices) and weights[k] finite and >= 0 (checked on the device:
+ * LB_ERR_INVALID_ARG otherwise).  Every iteration relaxes the out-edges of the
+ * frontier's vertices (groups of group_size threads, a power of two in
+ * [4, 256], 0 = 32) with an atomic minimum on the distance; a vertex whose
+ * distance dropped joins the next frontier once; the host loops until the
+ * frontier is empty.  dist (device, float [num_vertices], written): 0 at the
+ * source, +inf where unreachable, otherwise the least fixed point of
+ * dist[v] = min over edges (u, v) of fl32(dist[u] + w) -- deterministic.
+ * *host_iterations (nullable) gets the number of iterations.  Allocates
+ * 16 bytes per vertex of scratch and synchronises `stream` every iteration.
+ */
+lb_status_t lb_sssp(const int32_t* tile_offsets, int32_t num_vertices, int32_t num_edges, const int32_t* col_idx,
+                    const float* weights, int32_t source, int32_t group_size, float* dist, int32_t* host_iterations,
+                    void* stream);
 /* -------------------------------------------------------------- batching -- */
 
 /*

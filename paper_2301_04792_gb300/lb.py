@@ -274,6 +274,24 @@ def autotune(tile_offsets: torch.Tensor, col_idx: torch.Tensor, vals: torch.Tens
     return Plan._adopt(h, tile_offsets, N, C), report
 
 
+def sssp(tile_offsets: torch.Tensor, col_idx: torch.Tensor, weights: torch.Tensor, source: int, group_size: int = 0,
+         dist: torch.Tensor | None = None, stream=None):
+    """Single-source shortest paths (``lb_sssp``, Listing 5): returns (dist, iterations)."""
+    lib = _lib.load()
+    _need(tile_offsets, torch.int32, "tile_offsets")
+    V = tile_offsets.numel() - 1
+    E = int(col_idx.numel())
+    _need(col_idx, torch.int32, "col_idx")
+    _need(weights, torch.float32, "weights", E)
+    if dist is None:
+        dist = torch.empty(V, dtype=torch.float32, device=tile_offsets.device)
+    _need(dist, torch.float32, "dist", V)
+    it = ctypes.c_int32(0)
+    check(lib.lb_sssp(_ptr(tile_offsets), V, E, _ptr(col_idx), _ptr(weights), int(source), int(group_size),
+                      _ptr(dist), ctypes.byref(it), ctypes.c_void_p(_stream(stream))), "lb_sssp")
+    return dist, int(it.value)
+
+
 def autotune_cache_clear():
     _lib.load().lb_autotune_cache_clear()
 
