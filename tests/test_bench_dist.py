@@ -49,3 +49,13 @@ def test_single_rank_defaults(monkeypatch):
     assert bench.dist_env() == (1, 0, 0)
     assert bench.max_over_ranks(3.25, 1) == 3.25
     assert bench.spmv_bytes(2, 3, 5) == 8 * 5 + 4 * 3 + 4 * 3 + 4 * 2
+
+
+def test_bench_reads_traffic_from_the_committed_profile():
+    """roofline.traffic comes from the committed ncu summary while it matches the kernel source."""
+    import bench
+    t = bench.profiled_traffic()
+    if t is None:  # the kernels changed since the capture: the summary must say another hash
+        assert "kernel_source_sha: " + bench.kernel_source_sha() not in open(bench.PROFILE_SUMMARY).read()
+    else:
+        assert 150_000_000 < t < 250_000_000
