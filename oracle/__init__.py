@@ -56,6 +56,7 @@ def _bind(lib):
     f64p = ctypes.POINTER(ctypes.c_double)
     lib.or_spmv.argtypes = [ctypes.c_int32, i32p, i32p, f32p, f32p, f64p, f64p]
     lib.or_spmv_rows.argtypes = [ctypes.c_int64, i64p, i32p, i32p, f32p, f32p, f64p, f64p]
+    lib.or_coo_to_csr.argtypes = [ctypes.c_int32, ctypes.c_int64, i32p, i32p, i32p, i32p, i32p]
     lib.or_sssp.argtypes = [ctypes.c_int32, i32p, i32p, f32p, ctypes.c_int32, f32p]
     lib.or_sssp.restype = ctypes.c_int32
     lib.or_spmm.argtypes = [ctypes.c_int32, i32p, i32p, f32p, f32p, ctypes.c_int64, ctypes.c_int32, f64p, f64p]
@@ -211,6 +212,26 @@ class Oracle:
                               _p(cp, ctypes.c_int32), _p(riT, ctypes.c_int32), _p(perm, ctypes.c_int32))
         return cp, riT, perm
 
+    def coo_to_csr(self, num_rows, row, col, val):
+        """(rp, ci, v) of the COO atoms (row[k], col[k], val[k]) as a CSR tile set; atoms of a
+        row keep their input order."""
+        row, col, val = _c(row, np.int32), _c(col, np.int32), _c(val, np.float32)
+        N = row.shape[0]
+        rp = np.empty(num_rows + 1, dtype=np.int32)
+        ci = np.empty(N, dtype=np.int32)
+        perm = np.empty(N, dtype=np.int32)
+        self.lib.or_coo_to_csr(int(num_rows), N, _p(row, ctypes.c_int32), _p(col, ctypes.c_int32),
+                               _p(rp, ctypes.c_int32), _p(ci, ctypes.c_int32), _p(perm, ctypes.c_int32))
+        return rp, ci, val[perm]
+
+    def csc_to_csr(self, num_rows, cp, ri, val):
+        """(rp, ci, v) of a CSC matrix (column offsets cp, row ids ri) as a CSR tile set: the
+        CSC arrays read as the CSR of A^T, transposed by the stable counting sort (columns
+        ascend within each row)."""
+        cp, ri, val = _c(cp, np.int32), _c(ri, np.int32), _c(val, np.float32)
+        rp, ci, perm = self.transpose(cp, ri, num_rows)
+        return rp, ci, val[perm]
+
     def grad(self, rp, ci, v, x, dy, num_cols, want_dx=True, want_dvals=True):
         """(dx64, bx, dvals32) for L = dy . (A x)."""
         rp, ci, v, x, dy = (_c(rp, np.int32), _c(ci, np.int32), _c(v, np.float32), _c(x, np.float32),
@@ -281,6 +302,14 @@ def transpose(rp, ci, num_cols):
 
 def grad(rp, ci, v, x, dy, num_cols, want_dx=True, want_dvals=True):
     return default().grad(rp, ci, v, x, dy, num_cols, want_dx, want_dvals)
+
+
+def coo_to_csr(num_rows, row, col, val):
+    return default().coo_to_csr(num_rows, row, col, val)
+
+
+def csc_to_csr(num_rows, cp, ri, val):
+    return default().csc_to_csr(num_rows, cp, ri, val)
 
 
 def source_path() -> str:

@@ -282,3 +282,26 @@ int32_t or_sssp(int32_t V, const int32_t* rp, const int32_t* ci, const float* w,
   free(done);
   return settled;
 }
+
+/*
+ * COO -> CSR tile set ("other formats only need their own atom and tile
+ * iterators", Sec. 4): the tiles are the rows, so the tile offsets are the
+ * run lengths of the atoms' row ids, prefix-summed, and the atoms are placed
+ * by a stable counting sort on the row id (atoms of a row keep their input
+ * order).  rp[R+1]; perm[p] = input atom of CSR slot p; col_out[p] = its column.
+ * Row ids must lie in [0, R).
+ */
+void or_coo_to_csr(int32_t R, int64_t N, const int32_t* row, const int32_t* col, int32_t* rp, int32_t* col_out,
+                   int32_t* perm) {
+  for (int32_t r = 0; r <= R; ++r) rp[r] = 0;
+  for (int64_t k = 0; k < N; ++k) rp[row[k] + 1]++;
+  for (int32_t r = 0; r < R; ++r) rp[r + 1] += rp[r];
+  int32_t* cur = (int32_t*)malloc(sizeof(int32_t) * (size_t)(R > 0 ? R : 1));
+  for (int32_t r = 0; r < R; ++r) cur[r] = rp[r];
+  for (int64_t k = 0; k < N; ++k) {
+    int32_t p = cur[row[k]]++;
+    perm[p] = (int32_t)k;
+    col_out[p] = col[k];
+  }
+  free(cur);
+}

@@ -375,6 +375,39 @@ def test_sssp_against_bellman_ford_bfs_and_fp64_dijkstra():
     check_sssp(oracle.default())
 
 
+def check_formats(orc):
+    """COO and CSC inputs as CSR tile sets: the same dense matrix, rows in order, a row's atoms in
+    input order (COO) or ascending column (CSC), and round trips CSR -> COO -> CSR, CSR -> CSC -> CSR."""
+    rng = np.random.default_rng(31)
+    for R, C, N in ((0, 4, 0), (1, 1, 1), (5, 7, 0), (9, 6, 30), (40, 33, 500), (64, 64, 2000)):
+        row = rng.integers(0, max(R, 1), N).astype(np.int32) if R else np.zeros(0, np.int32)
+        col = rng.integers(0, C, N).astype(np.int32)
+        val = rng.uniform(-1, 1, N).astype(np.float32)
+        rp, ci, v = orc.coo_to_csr(R, row, col, val)
+        assert rp[0] == 0 and rp[-1] == N and (np.diff(rp) >= 0).all()
+        D = np.zeros((R, C))
+        np.add.at(D, (row, col), val.astype(np.float64))
+        assert np.array_equal(dense_of(rp, ci, v, C), D)
+        order = np.argsort(row, kind="stable")           # stable by row: the input order within a row
+        assert np.array_equal(ci, col[order]) and np.array_equal(v, val[order])
+        # CSR -> COO (expand the row ids) -> CSR is the identity
+        r2 = np.repeat(np.arange(R, dtype=np.int32), np.diff(rp))
+        rp2, ci2, v2 = orc.coo_to_csr(R, r2, ci, v)
+        assert np.array_equal(rp2, rp) and np.array_equal(ci2, ci) and np.array_equal(v2, v)
+        # CSC of the same matrix (sorted by column, rows ascending) -> CSR
+        oc = np.lexsort((row, col))
+        cp = np.concatenate([[0], np.cumsum(np.bincount(col, minlength=C))]).astype(np.int32)
+        rp3, ci3, v3 = orc.csc_to_csr(R, cp, row[oc], val[oc])
+        assert np.array_equal(dense_of(rp3, ci3, v3, C), D)
+        for r in range(R):
+            seg = ci3[rp3[r]:rp3[r + 1]]
+            assert (np.diff(seg) >= 0).all()              # columns ascend within a row
+
+
+def test_coo_and_csc_inputs():
+    check_formats(oracle.default())
+
+
 # ------------------------------------------------------------ mutation tests --
 
 MUTANTS = {
@@ -398,6 +431,9 @@ MUTANTS = {
     "dx_sign": ("dx[ci[k]] += p;", "dx[ci[k]] -= p;", check_grad),
     # SSSP relaxing with a dropped weight (distance of the source carried unchanged)
     "sssp_dropped_weight": ("float nd = dist[it.v] + w[k];", "float nd = dist[it.v] + 0.0f * w[k];", check_sssp),
+    # COO rows placed unstably (atoms of a row reversed)
+    "coo_unstable": ("int32_t p = cur[row[k]]++;", "int32_t p = rp[row[k] + 1] - 1 - (cur[row[k]]++ - rp[row[k]]);",
+                     check_formats),
     # wrong column of B in SpMM: the columns of B read in reverse order
     "spmm_wrong_b_column": ("(double)B[(int64_t)ci[k] * ldb + j];", "(double)B[(int64_t)ci[k] * ldb + (K - 1 - j)];",
                             check_spmm),
