@@ -336,6 +336,31 @@ lb_status_t lb_spmm(lb_plan_t plan, int32_t K, const int32_t* col_idx, const flo
 /* Builds the SpMM table and carry slots of a merge-path plan (allocates, synchronises `stream`);
  * nothing to do for a thread-mapped plan. */
 lb_status_t lb_prepare_spmm(lb_plan_t plan, void* stream);
+/* --------------------------------------------------------- input formats -- */
+/*
+ * COO -> CSR tile set (Sec. 4: a format needs only its own atom and tile
+ * iterators).  The tiles are the rows: tile_offsets_out[num_rows + 1] are the
+ * prefix-summed run lengths of row_idx, and the atoms (row_idx[k],
+ * col_idx[k], vals[k]), in any order, are placed by a stable counting sort on
+ * the row id, so a row's atoms keep their input order (an already row-sorted
+ * COO comes out unchanged).  Outputs: col_idx_out, vals_out [num_atoms].  All
+ * device pointers, caller-owned.  LB_ERR_INVALID_ARG for a row id outside
+ * [0, num_rows) (checked on the device).  Allocates scratch, synchronises.
+ */
+lb_status_t lb_coo_to_csr(int32_t num_rows, int32_t num_atoms, const int32_t* row_idx, const int32_t* col_idx,
+                          const float* vals, int32_t* tile_offsets_out, int32_t* col_idx_out, float* vals_out,
+                          void* stream);
+/*
+ * CSC -> CSR tile set: col_offsets[num_cols + 1] / row_idx / vals are read as
+ * the CSR of A^T; every atom's column comes from the merge-path atom-to-tile
+ * walk over col_offsets (validated: LB_ERR_INVALID_ARG if malformed), then the
+ * stable counting sort on the row id gives A's CSR (columns ascending within a
+ * row when they ascend in the CSC order).  LB_ERR_INVALID_ARG for a row id
+ * outside [0, num_rows).  Allocates scratch, synchronises.
+ */
+lb_status_t lb_csc_to_csr(int32_t num_rows, int32_t num_cols, int32_t num_atoms, const int32_t* col_offsets,
+                          const int32_t* row_idx, const float* vals, int32_t* tile_offsets_out, int32_t* col_idx_out,
+                          float* vals_out, void* stream);
 /* ------------------------------------------------------------------ SSSP -- */
 /*
  * Single-source shortest paths (Sec. 7, Listing 5) on the group-mapped

@@ -9,7 +9,7 @@ differentiable backward and a batched persistent form.  The compute lives in
 """
 from .buildlib import build  # noqa: F401
 from .lb import (BatchPlan, LBBatchSpMV, LBSpMV, Plan, Schedule, autotune, autotune_cache_clear,  # noqa: F401
-                 batch_spmv, heuristic_schedule, merge_diagonals, spmv, sssp)
+                 batch_spmv, coo_to_csr, csc_to_csr, heuristic_schedule, merge_diagonals, spmv, sssp)
 
 __all__ = ["build", "Plan", "BatchPlan", "Schedule", "LBSpMV", "LBBatchSpMV", "spmv", "batch_spmv",
-           "heuristic_schedule", "merge_diagonals", "autotune", "autotune_cache_clear", "sssp"]
+           "heuristic_schedule", "merge_diagonals", "autotune", "autotune_cache_clear", "sssp", "coo_to_csr", "csc_to_csr"]

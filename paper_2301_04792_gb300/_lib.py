@@ -84,6 +84,8 @@ SIGNATURES = {
     "lb_autotune": (I32, [VP, I32, I32, VP, VP, VP, VP, ctypes.POINTER(TuneOpts), ctypes.POINTER(TuneResult), PLANP,
                           VP]),
     "lb_autotune_cache_clear": (None, []),
+    "lb_coo_to_csr": (I32, [I32, I32, VP, VP, VP, VP, VP, VP, VP]),
+    "lb_csc_to_csr": (I32, [I32, I32, I32, VP, VP, VP, VP, VP, VP, VP]),
     "lb_sssp": (I32, [VP, I32, I32, VP, VP, I32, I32, VP, ctypes.POINTER(I32), VP]),
     "lb_spmm": (I32, [VP, I32, VP, VP, VP, I64, VP, I64, VP]),
     "lb_prepare_spmm": (I32, [VP, VP]),

@@ -274,6 +274,39 @@ def autotune(tile_offsets: torch.Tensor, col_idx: torch.Tensor, vals: torch.Tens
     return Plan._adopt(h, tile_offsets, N, C), report
 
 
+def coo_to_csr(num_rows: int, row_idx: torch.Tensor, col_idx: torch.Tensor, vals: torch.Tensor, stream=None):
+    """(tile_offsets, col_idx, vals) of a COO matrix as a CSR tile set (``lb_coo_to_csr``)."""
+    lib = _lib.load()
+    N = int(row_idx.numel())
+    _need(row_idx, torch.int32, "row_idx")
+    _need(col_idx, torch.int32, "col_idx", N)
+    _need(vals, torch.float32, "vals", N)
+    dev = row_idx.device
+    rp = torch.empty(int(num_rows) + 1, dtype=torch.int32, device=dev)
+    ci = torch.empty(N, dtype=torch.int32, device=dev)
+    v = torch.empty(N, dtype=torch.float32, device=dev)
+    check(lib.lb_coo_to_csr(int(num_rows), N, _ptr(row_idx), _ptr(col_idx), _ptr(vals), _ptr(rp), _ptr(ci), _ptr(v),
+                            ctypes.c_void_p(_stream(stream))), "lb_coo_to_csr")
+    return rp, ci, v
+
+
+def csc_to_csr(num_rows: int, col_offsets: torch.Tensor, row_idx: torch.Tensor, vals: torch.Tensor, stream=None):
+    """(tile_offsets, col_idx, vals) of a CSC matrix as a CSR tile set (``lb_csc_to_csr``)."""
+    lib = _lib.load()
+    _need(col_offsets, torch.int32, "col_offsets")
+    C = col_offsets.numel() - 1
+    N = int(row_idx.numel())
+    _need(row_idx, torch.int32, "row_idx")
+    _need(vals, torch.float32, "vals", N)
+    dev = col_offsets.device
+    rp = torch.empty(int(num_rows) + 1, dtype=torch.int32, device=dev)
+    ci = torch.empty(N, dtype=torch.int32, device=dev)
+    v = torch.empty(N, dtype=torch.float32, device=dev)
+    check(lib.lb_csc_to_csr(int(num_rows), C, N, _ptr(col_offsets), _ptr(row_idx), _ptr(vals), _ptr(rp), _ptr(ci),
+                            _ptr(v), ctypes.c_void_p(_stream(stream))), "lb_csc_to_csr")
+    return rp, ci, v
+
+
 def sssp(tile_offsets: torch.Tensor, col_idx: torch.Tensor, weights: torch.Tensor, source: int, group_size: int = 0,
          dist: torch.Tensor | None = None, stream=None):
     """Single-source shortest paths (``lb_sssp``, Listing 5): returns (dist, iterations)."""
