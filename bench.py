@@ -687,6 +687,59 @@ def run_ours(args, ws, rank, local):
         dist.destroy_process_group()
 
 
+PROFILE_CASES = ("lookback_rmat", "thread_mapped_powerlaw", "block_mapped_powerlaw", "spmm_k32_powerlaw",
+                 "sssp_rmat", "batch_fwd_bwd_diff4")
+
+
+def run_case(name: str):
+    """A few launches of one kernel family on its workload, for an ncu capture (no timing, no JSON)."""
+    import torch
+    import paper_2301_04792_gb300 as lb
+    import workloads as W
+    lb.build()
+    dev = torch.device("cuda")
+
+    def d(*arrays):
+        return [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in arrays]
+
+    if name == "sssp_rmat":
+        g = W.rmat()
+        rp, ci, w = d(g.rp, g.ci, g.v.astype(np.float32))
+        lb.sssp(rp, ci, w, 0, group_size=256)
+    elif name == "batch_fwd_bwd_diff4":
+        b = W.diff_batch(num=4)
+        rows, cols, nnz = b.rows(), b.cols(), b.nnz()
+        rp_cat, ci, v = d(b.rp_cat(), b.ci_cat(), b.v_cat())
+        x = torch.rand(int(cols.sum()), device=dev)
+        dy = torch.rand(int(rows.sum()), device=dev)
+        bp = lb.BatchPlan(rows, cols, nnz, rp_cat, mp_variant=3, items_per_thread=4)
+        bp.prepare_backward(ci)
+        for _ in range(3):
+            bp.spmv(ci, v, x)
+            bp.backward(ci, v, x, dy)
+    else:
+        m = W.rmat() if name == "lookback_rmat" else W.powerlaw()
+        rp, ci, v = d(m.rp, m.ci, m.v)
+        x = torch.rand(m.num_cols, device=dev)
+        y = torch.empty(m.num_rows, device=dev)
+        if name == "lookback_rmat":
+            p = lb.Plan(rp, m.nnz, "merge_path", num_cols=m.num_cols, items_per_thread=4, mp_variant=3)
+        elif name == "thread_mapped_powerlaw":
+            p = lb.Plan(rp, m.nnz, "thread_mapped")
+        elif name == "block_mapped_powerlaw":
+            p = lb.Plan(rp, m.nnz, "block_mapped")
+        else:
+            p = lb.Plan(rp, m.nnz, "merge_path", num_cols=m.num_cols)
+            B = torch.rand(m.num_cols, 32, device=dev)
+            C = torch.empty(m.num_rows, 32, device=dev)
+        for _ in range(3):
+            if name == "spmm_k32_powerlaw":
+                p.spmm(ci, v, B, C)
+            else:
+                p.spmv(ci, v, x, y)
+    torch.cuda.synchronize()
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -700,7 +753,12 @@ def main(argv=None):
     ap.add_argument("--quick", action="store_true", help="skip the other schedules")
     ap.add_argument("--ncu", action="store_true",
                     help="profiling run: only the timed launches (no load loop, schedules, batch or CPU leg)")
+    ap.add_argument("--case", choices=PROFILE_CASES,
+                    help="run a few launches of one kernel family for an ncu capture, then exit")
     args = ap.parse_args(argv)
+    if args.case:
+        run_case(args.case)
+        return
     ws, rank, local = dist_env()
     if args.warmup < 3:
         args.warmup = 3
