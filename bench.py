@@ -746,7 +746,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--ipt", type=int, default=8, help="merge-path items per thread (4, 8, 16)")
+    ap.add_argument("--ipt", type=int, default=4, help="merge-path items per thread (4, 8, 16)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

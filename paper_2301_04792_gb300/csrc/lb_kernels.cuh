@@ -1043,7 +1043,7 @@ struct WarpWalker {
 // segmented scan over the 8 warps' carries keyed by row) and leaves one
 // carry; the last CTA to finish combines those in order.
 template <int IPT, bool XB, bool PERM, bool VEC>
-__global__ void __launch_bounds__(256, IPT <= 8 ? 4 : 2) mp_spmv_warp_kernel(MpArgs a) {
+__global__ void __launch_bounds__(256, IPT <= 4 ? 5 : IPT <= 8 ? 4 : 2) mp_spmv_warp_kernel(MpArgs a) {
   constexpr int WPB = 8;
   __shared__ WarpScratch<IPT> sc_all[WPB];
   __shared__ float s_wv[WPB];
