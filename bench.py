@@ -245,6 +245,110 @@ def time_launches(torch, launch, n, stream):
     return [s.elapsed_time(e) for s, e in zip(starts, ends)]
 
 
+def bench_configs(torch, lb, W, device, peak, cores):
+    """Every workload's fastest schedule (autotuner, cold L2) with the oracle on 1 and all host cores;
+    the 512-matrix batch as one graph-replayed launch against per-matrix launches."""
+    import oracle
+    out = {}
+    for name, gen in (("plain_2000", W.plain), ("powerlaw_1M", W.powerlaw), ("rmat_scale22", W.rmat),
+                      ("stencil27_160", W.stencil27)):
+        m = gen()
+        rp, ci, v = (torch.from_numpy(a).to(device) for a in (m.rp, m.ci, m.v))
+        x_np = W.x_for(m)
+        x = torch.from_numpy(x_np).to(device)
+        _, rep = lb.autotune(rp, ci, v, x, num_cols=m.num_cols, reps=7, cold_l2=True, use_cache=False)
+        best = next(c for c in rep["candidates"] if c["name"] == rep["best"])
+        byts = spmv_bytes(m.num_rows, m.num_cols, m.nnz)
+        y64, b = oracle.spmv(m.rp, m.ci, m.v, x_np)
+        ok = bool((np.abs(rep["y"].cpu().numpy().astype(np.float64) - y64) <= oracle.TOL * b).all())
+        t1 = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            oracle.spmv(m.rp, m.ci, m.v, x_np)
+            t1.append(time.perf_counter() - t0)
+        tn = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            oracle.spmv_threads(m.rp, m.ci, m.v, x_np, cores)
+            tn.append(time.perf_counter() - t0)
+        gbps = byts / (best["ms"] * 1e-3) / 1e9
+        out[name] = {"rows": m.num_rows, "nnz": m.nnz, "best": rep["best"], "us": round(best["ms"] * 1e3, 2),
+                     "GBps": round(gbps, 2), "frac_of_8TBps": round(gbps / 8000.0, 4),
+                     "frac_of_measured": round(gbps / peak, 4), "GFLOPs": round(2 * m.nnz / (best["ms"] * 1e-3) / 1e9, 2),
+                     "parity_all_rows": ok, "oracle_1core_ms": round(statistics.median(t1) * 1e3, 3),
+                     f"oracle_{cores}core_ms": round(statistics.median(tn) * 1e3, 3)}
+        del rp, ci, v, x
+    # the 512-matrix batch: one persistent launch (graph) vs one launch per matrix
+    b = W.batch()
+    rows, cols, nnz = b.rows(), b.cols(), b.nnz()
+    rp_cat = torch.from_numpy(b.rp_cat()).to(device)
+    ci = torch.from_numpy(b.ci_cat()).to(device)
+    v = torch.from_numpy(b.v_cat()).to(device)
+    x = torch.rand(int(cols.sum()), device=device)
+    y = torch.empty(int(rows.sum()), device=device)
+    bp = lb.BatchPlan(rows, cols, nnz, rp_cat, mp_variant=3, items_per_thread=4)
+    rb = np.concatenate([[0], np.cumsum(rows)])
+    cb = np.concatenate([[0], np.cumsum(cols)])
+    nb = np.concatenate([[0], np.cumsum(nnz)])
+    plans = [lb.Plan(rp_cat[rb[i] + i: rb[i + 1] + i + 1], int(nnz[i]), "merge_path", num_cols=int(cols[i]))
+             for i in range(b.num)]
+    import ctypes
+    from paper_2301_04792_gb300 import _lib
+    lib = _lib.load()
+    vp = ctypes.c_void_p
+    calls = [(p.handle, vp(ci.data_ptr() + 4 * int(nb[i])), vp(v.data_ptr() + 4 * int(nb[i])),
+              vp(x.data_ptr() + 4 * int(cb[i])), vp(y.data_ptr() + 4 * int(rb[i]))) for i, p in enumerate(plans)]
+
+    def per_matrix(sp):
+        for h, c_, v_, x_, y_ in calls:
+            _lib.check(lib.lb_spmv(h, c_, v_, x_, y_, vp(sp)), "lb_spmv")
+    s = torch.cuda.Stream(device=device)
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(2):
+            bp.spmv(ci, v, x, y)
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        bp.spmv(ci, v, x, y)
+    gp = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream(device=device)
+    with torch.cuda.graph(gp, stream=cap):
+        per_matrix(cap.cuda_stream)
+    torch.cuda.synchronize()
+
+    def timed(fn, reps=7):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+    t_b = timed(g.replay)
+    t_p = timed(lambda: per_matrix(torch.cuda.current_stream(device).cuda_stream))
+    t_pg = timed(gp.replay)
+    R, C, N = int(rows.sum()), int(cols.sum()), int(nnz.sum())
+    byts = 8 * N + 4 * (R + b.num) + 4 * C + 4 * R
+    gbps = byts / (t_b * 1e-3) / 1e9
+    out["batch512"] = {"rows": R, "nnz": N, "batched_graph_ms": round(t_b, 4), "per_matrix_ms": round(t_p, 4),
+                       "per_matrix_graph_ms": round(t_pg, 4), "speedup": round(t_p / t_b, 3),
+                       "speedup_vs_graph": round(t_pg / t_b, 3), "GBps": round(gbps, 2),
+                       "frac_of_8TBps": round(gbps / 8000.0, 4), "frac_of_measured": round(gbps / peak, 4),
+                       "GFLOPs": round(2 * N / (t_b * 1e-3) / 1e9, 2),
+                       "batch_plan": "merge_path_ipt4_v3", "per_matrix_plan": "merge_path_ipt8_v0 (library default)"}
+    for p in plans:
+        p.close()
+    bp.close()
+    del g, gp
+    torch.cuda.synchronize()
+    return out
+
+
 def bench_batched(torch, lb, W, device, reps=5):
     """Per-matrix fwd+bwd launches vs. batched persistent launches replayed from a CUDA graph."""
     b = W.diff_batch()
@@ -617,6 +721,10 @@ def run_ours(args, ws, rank, local):
     if not args.no_batch and not args.ncu:
         batched = bench_batched(torch, lb, W, device)
 
+    configs = None
+    if not args.quick and not args.ncu and not args.no_batch:
+        configs = bench_configs(torch, lb, W, device, peak, host_cores())
+
     # SSSP (Listing 5) on the R-MAT graph from vertex 0, weights U(0,1)
     sssp = None
     if not args.quick and not args.ncu:
@@ -672,6 +780,7 @@ def run_ours(args, ws, rank, local):
             "autotune": tune,
             "spmm_merge_path": spmm,
             "sssp_group_mapped": sssp,
+            "configs": configs,
             "schedules_GBps": sched,
             "e2e": {"value": round(e2e_val, 2), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": round(e2e_ms, 4), "ok": e2e_ok},
