@@ -88,9 +88,10 @@ typedef struct lb_plan_opts_t {
                                merge order from a counter, each share's carry resolved by a decoupled
                                look-back over the preceding shares' published partial sums (no block
                                barrier, no fix-up pass; bounded waits report LB_ERR_TIMEOUT) */
-  int32_t wave_items;       /* batches, warp workers: minimum rows + atoms of a wave (a run of whole
-                               matrices shared out over all workers before the next run starts; keeps
-                               the run's vectors in L2); 0 = max(4 Mi, 2 x workers x items_per_tile) */
+  int32_t wave_items;       /* batches, mp_variant 0: minimum rows + atoms of a wave (a run of whole
+                               matrices shared out over all warps before the next run starts; keeps
+                               the run's vectors in L2); 0 = max(4 Mi, 2 x launched warps x items_per_tile).
+                               mp_variant 3 needs no waves: its shares are taken in merge order */
   int32_t units_per_cta;    /* merge-path, warp workers: the rows + atoms are cut into this many equal
                                work units per launched CTA (8 warp shares each), which the CTAs take in
                                merge order from a counter, so a CTA that finishes early takes more work
