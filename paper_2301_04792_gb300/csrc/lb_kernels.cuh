@@ -1181,20 +1181,24 @@ __device__ __forceinline__ bool look_back(const unsigned long long* records, int
 template <int IPT, bool XB, bool PERM, bool VEC>
 __global__ void __launch_bounds__(256, IPT <= 8 ? 4 : 2) mp_spmv_lookback_kernel(MpArgs a) {
   constexpr int WPB = 8;
+  constexpr int kNarrow = 4;  // predecessors one lane walks before the warp-wide window takes over
   __shared__ WarpScratch<IPT> sc_all[WPB];
+  __shared__ int s_pend[WPB][32];  // shares whose first row waits for its predecessors' sums
   __shared__ int s_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   WarpWalker<IPT, XB, PERM, VEC> wk(a, sc_all[warp]);
   const unsigned epoch = *reinterpret_cast<volatile unsigned*>(a.ticket + 2);
-  // the first row of share p (still needing its predecessors' sums) gets them
+  auto add_to_first_row = [&](int p, float total) {
+    float* py = a.out + __ldg(&a.share_head[p].x);
+    __stcg(py, __ldcg(py) + total);
+  };
+  // the first row of share p gets its predecessors' sums: the warp-wide window
   auto resolve = [&](int p) {
     float total;
     if (!look_back(a.records, p, epoch, total) && lane == 0 && a.status) atomicOr(a.status, kDevErrTimeout);
-    if (lane == 0) {
-      float* py = a.out + __ldg(&a.share_head[p].x);
-      __stcg(py, __ldcg(py) + total);
-    }
+    if (lane == 0) add_to_first_row(p, total);
   };
+  int npend = 0;
 
   int s = 0;
   if (lane == 0) s = (int)atomicAdd(a.ticket + 1, 1u);
@@ -1227,7 +1231,6 @@ __global__ void __launch_bounds__(256, IPT <= 8 ? 4 : 2) mp_spmv_lookback_kernel
   float carry = 0.f;
   int next = 0;         // lane 0: the share after s, taken two tiles before its end
   bool taken = false;
-  int pend = -1;        // share whose first row still needs its predecessors' sums
   while (s < a.num_workers) {
     if (!taken && e + 1 >= e_last) {
       if (lane == 0) next = (int)atomicAdd(a.ticket + 1, 1u);
@@ -1262,8 +1265,17 @@ __global__ void __launch_bounds__(256, IPT <= 8 ? 4 : 2) mp_spmv_lookback_kernel
     // share s is done; c1 is its end, its head holds its first row
     const bool has_end = c1.x > __ldg(&a.share_head[s].x);
     if (lane == 0 && s + 1 < a.num_workers) publish_record(a.records + s, epoch, has_end, carry);
-    if (pend >= 0) resolve(pend);
-    pend = (has_end && s > 0) ? s : -1;
+    // resolved once the warp has no shares left (the records are published by then), one lane per
+    // pending share; a full list is resolved at once
+    if (has_end && s > 0) {
+      if (npend == 32) {
+        for (int q = 0; q < 32; ++q) resolve(s_pend[warp][q]);
+        npend = 0;
+      }
+      if (lane == 0) s_pend[warp][npend] = s;
+      ++npend;
+      __syncwarp();
+    }
     // on to share sn, its first tile already loading (head and entry base
     // read again: cached since the loads above)
     s = sn;
@@ -1277,7 +1289,34 @@ __global__ void __launch_bounds__(256, IPT <= 8 ? 4 : 2) mp_spmv_lookback_kernel
     carry = 0.f;
     taken = false;
   }
-  if (pend >= 0) resolve(pend);
+  // Each lane walks back from one pending share through the records, nearest first, adding the
+  // partial sums up to the nearest FINAL one (or share 0); a run longer than kNarrow records goes to
+  // the warp-wide window instead.  Either way the order of the sums depends only on the data.
+  bool wide = false;
+  if (lane < npend) {
+    const int p = s_pend[warp][lane];
+    float total = 0.f;
+    bool done = false, gave_up = false;
+    for (int q = p - 1, n = 0; q >= 0 && n < kNarrow && !done && !gave_up; --q, ++n) {
+      unsigned long long w = 0;
+      for (long long spin = 0;; ++spin) {
+        w = *reinterpret_cast<volatile const unsigned long long*>(a.records + q);
+        if ((unsigned)(w >> 33) == epoch) break;
+        if (spin > kLookbackSpins) {
+          gave_up = true;
+          break;
+        }
+        __nanosleep(64);
+      }
+      if (gave_up) break;
+      total += __uint_as_float((unsigned)w);
+      done = ((w >> 32) & 1ull) || q == 0;
+    }
+    if (gave_up && a.status) atomicOr(a.status, kDevErrTimeout);
+    if (done || gave_up) add_to_first_row(p, total);
+    else wide = true;
+  }
+  for (unsigned m = __ballot_sync(kFull, wide); m; m &= m - 1) resolve(s_pend[warp][__ffs(m) - 1]);
   // the last CTA to finish resets the share counter and advances the epoch
   if (cta_ticket(a, &s_last) && threadIdx.x == 0) {
     const unsigned e1 = (epoch + 1u) & 0x7fffffffu;
