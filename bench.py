@@ -403,6 +403,7 @@ def bench_batched(torch, lb, W, device, reps=5):
         return plans, calls, runner
 
     plain_cfgs = {"merge_path_ipt8_v0": dict(items_per_thread=8, mp_variant=0),
+                  "merge_path_ipt4_v0": dict(items_per_thread=4, mp_variant=0),
                   "merge_path_ipt4_v3": dict(items_per_thread=4, mp_variant=3)}
     plains = {k: make_plain(**kw) for k, kw in plain_cfgs.items()}
 
