@@ -883,8 +883,10 @@ struct WarpSplits {
 // start gets only this share's part; walk() returns the split at the share's
 // end, with the partial sum of the row left open there in `carry`.
 // VEC: idx and val (or perm) are 16-byte aligned (vector loads); otherwise
-// every atom is loaded on its own.
-template <int IPT, bool XB, bool PERM, bool VEC>
+// every atom is loaded on its own.  ONE_ROW: a tile inside a single row is
+// summed without the row pass and the segmented scan (the look-back kernel,
+// whose guided shares gain from it; the static kernel measured faster without).
+template <int IPT, bool XB, bool PERM, bool VEC, bool ONE_ROW = false>
 struct WarpWalker {
   static_assert(IPT % 4 == 0 && 32 % IPT == 0, "IPT must be 4, 8 or 16");
   const MpArgs& a;
@@ -957,6 +959,17 @@ struct WarpWalker {
   __device__ __forceinline__ void reduce_tile(int2 t0, int2 t1, int e_t, const float (&xg)[IPT],
                                               const float (&vv)[IPT], float& carry) {
     const int nrows = t1.x - t0.x, j0 = t0.y, off = j0 & 3;
+    if (ONE_ROW && nrows == 0) {
+      // the tile lies inside one row (the usual case in long rows): no row ends, so its products
+      // are one sum -- each lane's in order, the lanes' by a fixed butterfly -- added to the carry
+      float acc = 0.f;
+#pragma unroll
+      for (int q = 0; q < IPT; ++q) acc += vv[q] * xg[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+      carry = carry + acc;
+      return;
+    }
     warp_row_pass<IPT, true>(a.rp, t0.x, nrows, j0, off, carry, e_t, sc);
     const float prefix = (nrows > 0 && __shfl_sync(kFull, e_t, 0) == j0) ? 0.f : carry;
     __syncwarp();
@@ -1186,7 +1199,7 @@ __global__ void __launch_bounds__(256, IPT <= 8 ? 4 : 2) mp_spmv_lookback_kernel
   __shared__ int s_pend[WPB][32];  // shares whose first row waits for its predecessors' sums
   __shared__ int s_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  WarpWalker<IPT, XB, PERM, VEC> wk(a, sc_all[warp]);
+  WarpWalker<IPT, XB, PERM, VEC, true> wk(a, sc_all[warp]);
   const unsigned epoch = *reinterpret_cast<volatile unsigned*>(a.ticket + 2);
   auto add_to_first_row = [&](int p, float total) {
     float* py = a.out + __ldg(&a.share_head[p].x);
