@@ -1401,23 +1401,29 @@ __global__ void __launch_bounds__(256) mp_expand_warp_kernel(MpArgs a) {
         if constexpr (DVALS) load_cols(c1, c2, c_cur);
         e_next = lane < c2.x - c1.x ? __ldg(a.rp + c1.x + 1 + lane) : 0;
       }
-      warp_row_pass<IPT, false>(a.rp, c0.x, nrows, j0, off, 0.f, e_cur, sc);
-      __syncwarp();
-      const unsigned bits = (sc.bits[s0 >> 5] >> (s0 & 31)) & (IPT == 32 ? 0xffffffffu : ((1u << IPT) - 1u));
-      // first marked slot of each later lane: suffix minimum over the lanes
-      int fm = bits ? s0 + __ffs(bits) - 1 : INT_MAX;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int n = __shfl_down_sync(kFull, fm, o);
-        if (lane + o < 32) fm = min(fm, n);
-      }
-      int nxt = __shfl_down_sync(kFull, fm, 1);
-      if (lane == 31) nxt = INT_MAX;
       int rows_q[IPT];
+      if (nrows == 0) {
+        // the tile lies inside one row: every atom is that row's
 #pragma unroll
-      for (int q = IPT - 1; q >= 0; --q) {
-        if ((bits >> q) & 1u) nxt = s0 + q;
-        rows_q[q] = nxt == INT_MAX ? c1.x : c0.x + sc.endrow[nxt];
+        for (int q = 0; q < IPT; ++q) rows_q[q] = c1.x;
+      } else {
+        warp_row_pass<IPT, false>(a.rp, c0.x, nrows, j0, off, 0.f, e_cur, sc);
+        __syncwarp();
+        const unsigned bits = (sc.bits[s0 >> 5] >> (s0 & 31)) & (IPT == 32 ? 0xffffffffu : ((1u << IPT) - 1u));
+        // first marked slot of each later lane: suffix minimum over the lanes
+        int fm = bits ? s0 + __ffs(bits) - 1 : INT_MAX;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int n = __shfl_down_sync(kFull, fm, o);
+          if (lane + o < 32) fm = min(fm, n);
+        }
+        int nxt = __shfl_down_sync(kFull, fm, 1);
+        if (lane == 31) nxt = INT_MAX;
+#pragma unroll
+        for (int q = IPT - 1; q >= 0; --q) {
+          if ((bits >> q) & 1u) nxt = s0 + q;
+          rows_q[q] = nxt == INT_MAX ? c1.x : c0.x + sc.endrow[nxt];
+        }
       }
 #pragma unroll
       for (int q = 0; q < IPT; ++q) {
