@@ -245,6 +245,31 @@ def time_launches(torch, launch, n, stream):
     return [s.elapsed_time(e) for s, e in zip(starts, ends)]
 
 
+def gather_probe_ms(torch, lib, ci, v, x, n, device, reps=7):
+    """Median time (ms) of lb_probe_gather over n atoms (streams col_idx/vals, gathers x, nothing else),
+    L2 flushed before every launch as in the autotuner's cold-L2 protocol."""
+    import ctypes
+    from paper_2301_04792_gb300 import _lib
+    vp = ctypes.c_void_p
+    n4 = n - (n % 4)
+    grid = lib.lb_probe_gather_grid()
+    out = torch.empty(max(1, grid) * 256, device=device)
+    flush = torch.empty(2 * torch.cuda.get_device_properties(device).L2_cache_size // 4, device=device)
+    sp = torch.cuda.current_stream(device)
+    ts = []
+    for i in range(reps + 2):
+        flush.fill_(float(i))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(sp)
+        _lib.check(lib.lb_probe_gather(vp(ci.data_ptr()), vp(v.data_ptr()), vp(x.data_ptr()), n4,
+                                       vp(out.data_ptr()), grid, vp(sp.cuda_stream)), "lb_probe_gather")
+        e1.record(sp)
+        torch.cuda.synchronize()
+        if i >= 2:
+            ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
 def bench_configs(torch, lb, W, device, peak, cores):
     """Every workload's fastest schedule (autotuner, cold L2) with the oracle on 1 and all host cores;
     the 512-matrix batch as one graph-replayed launch against per-matrix launches."""
@@ -272,7 +297,10 @@ def bench_configs(torch, lb, W, device, peak, cores):
             oracle.spmv_threads(m.rp, m.ci, m.v, x_np, cores)
             tn.append(time.perf_counter() - t0)
         gbps = byts / (best["ms"] * 1e-3) / 1e9
+        from paper_2301_04792_gb300 import _lib
+        probe = gather_probe_ms(torch, _lib.load(), ci, v, x, m.nnz, device)
         out[name] = {"rows": m.num_rows, "nnz": m.nnz, "best": rep["best"], "us": round(best["ms"] * 1e3, 2),
+                     "gather_ceiling_us": round(probe * 1e3, 2), "frac_of_gather_ceiling": round(probe / best["ms"], 4),
                      "GBps": round(gbps, 2), "frac_of_8TBps": round(gbps / 8000.0, 4),
                      "frac_of_measured": round(gbps / peak, 4), "GFLOPs": round(2 * m.nnz / (best["ms"] * 1e-3) / 1e9, 2),
                      "parity_all_rows": ok, "oracle_1core_ms": round(statistics.median(t1) * 1e3, 3),
@@ -808,7 +836,7 @@ def run_ours(args, ws, rank, local):
         dist.destroy_process_group()
 
 
-PROFILE_CASES = ("lookback_rmat", "thread_mapped_powerlaw", "block_mapped_powerlaw", "spmm_k32_powerlaw",
+PROFILE_CASES = ("lookback_rmat", "lookback_stencil", "thread_mapped_powerlaw", "block_mapped_powerlaw", "spmm_k32_powerlaw",
                  "sssp_rmat", "batch_fwd_bwd_diff4")
 
 
@@ -839,12 +867,14 @@ def run_case(name: str):
             bp.spmv(ci, v, x)
             bp.backward(ci, v, x, dy)
     else:
-        m = W.rmat() if name == "lookback_rmat" else W.powerlaw()
+        m = W.rmat() if name == "lookback_rmat" else W.stencil27() if name == "lookback_stencil" else W.powerlaw()
         rp, ci, v = d(m.rp, m.ci, m.v)
         x = torch.rand(m.num_cols, device=dev)
         y = torch.empty(m.num_rows, device=dev)
         if name == "lookback_rmat":
             p = lb.Plan(rp, m.nnz, "merge_path", num_cols=m.num_cols, items_per_thread=4, mp_variant=3)
+        elif name == "lookback_stencil":
+            p = lb.Plan(rp, m.nnz, "merge_path", num_cols=m.num_cols, items_per_thread=8, mp_variant=3)
         elif name == "thread_mapped_powerlaw":
             p = lb.Plan(rp, m.nnz, "thread_mapped")
         elif name == "block_mapped_powerlaw":
