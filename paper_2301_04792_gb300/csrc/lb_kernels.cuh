@@ -974,35 +974,31 @@ struct WarpWalker {
     const float prefix = (nrows > 0 && __shfl_sync(kFull, e_t, 0) == j0) ? 0.f : carry;
     __syncwarp();
     const unsigned bits = sc.bits[s0 >> 5] >> (s0 & 31);
+    // the lane's first row end keeps its partial sum for the scan; a later one (a row that
+    // lies inside the lane, rare) stores its sum at once; selects, no branch per slot
     float acc = 0.f, first = 0.f;
-    int any = 0, first_row = 0;
+    int first_q = -1;
 #pragma unroll
     for (int q = 0; q < IPT; ++q) {
       acc += vv[q] * xg[q];
-      if ((bits >> q) & 1u) {
-        const int r = sc.endrow[s0 + q];
-        if (any) {
-          sc.y[r] = acc;
-        } else {
-          first = acc;
-          first_row = r;
-          any = 1;
-        }
-        acc = 0.f;
-      }
+      const bool m = (bits >> q) & 1u;
+      if (m && first_q >= 0) sc.y[sc.endrow[s0 + q]] = acc;
+      first = (m && first_q < 0) ? acc : first;
+      first_q = (m && first_q < 0) ? q : first_q;
+      acc = m ? 0.f : acc;
     }
+    const int any = first_q >= 0;
+    const int first_row = any ? sc.endrow[s0 + first_q] : 0;
+    // segment heads at or below this lane: the scan adds lane - o only while no head lies in between
+    const unsigned heads = __ballot_sync(kFull, any) & (0xffffffffu >> (31 - lane));
+    const int head = heads ? 31 - __clz(heads) : -1;
     float v = acc;
-    int f = any;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const float vo = __shfl_up_sync(kFull, v, o);
-      const int fo = __shfl_up_sync(kFull, f, o);
-      if (lane >= o) {
-        if (!f) v = vo + v;
-        f |= fo;
-      }
+      if (lane >= o && lane - o >= head) v = vo + v;
     }
-    if (!f) v = prefix + v;
+    if (head < 0) v = prefix + v;
     const float up = __shfl_up_sync(kFull, v, 1);
     const float excl = lane ? up : prefix;
     carry = __shfl_sync(kFull, v, 31);
