@@ -432,6 +432,7 @@ def bench_batched(torch, lb, W, device, reps=5):
 
     plain_cfgs = {"merge_path_ipt8_v0": dict(items_per_thread=8, mp_variant=0),
                   "merge_path_ipt4_v0": dict(items_per_thread=4, mp_variant=0),
+                  "merge_path_ipt4_v0_w2": dict(items_per_thread=4, mp_variant=0, row_weight=2),
                   "merge_path_ipt4_v3": dict(items_per_thread=4, mp_variant=3)}
     plains = {k: make_plain(**kw) for k, kw in plain_cfgs.items()}
 
@@ -563,7 +564,7 @@ def run_ours(args, ws, rank, local):
                 _lib.check(st, "lb_spmv")
         return launch
 
-    plans = plans_for("merge_path", items_per_thread=args.ipt)
+    plans = plans_for("merge_path", items_per_thread=args.ipt, row_weight=args.row_weight)
     launch = launcher(plans)
     info = plans[0].info()
 
@@ -808,7 +809,8 @@ def run_ours(args, ws, rank, local):
             "warmup": args.warmup, "ms_per_step": round(step_ms, 5), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "powerlaw_1M", "rows": R, "cols": C, "nnz": N, "schedule": "merge_path",
-                       "items_per_thread": args.ipt, "grid": info["grid"], "tiles_per_cta": info["tiles_per_cta"],
+                       "items_per_thread": args.ipt, "row_weight": args.row_weight, "grid": info["grid"],
+                       "tiles_per_cta": info["tiles_per_cta"],
                        "bytes_per_step": byts, "l2": "inputs rotate over 4 copies (4 x %.0f MB > 4x L2)" % (byts / 1e6),
                        "l2_bytes": int(getattr(props, "L2_cache_size", 0)), "sms": int(props.multi_processor_count),
                        "parallelism": f"replicas x{ws}"},
@@ -898,6 +900,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--ipt", type=int, default=4, help="merge-path items per thread (4, 8, 16)")
+    ap.add_argument("--row-weight", type=int, default=2,
+                    help="merge-path shares: a row end counts as this many atoms (1 = equal rows + atoms)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -101,7 +101,13 @@ typedef struct lb_plan_opts_t {
   int32_t tiles_per_share;  /* merge-path variant 3: smallest look-back share in warp tiles (default 1) */
   int32_t items_per_thread_t; /* merge-path: items_per_thread of the transposed tile set (dx) built by
                                lb_prepare_backward / lb_batch_prepare_backward (0 = items_per_thread) */
-  int32_t reserved[2];
+  int32_t row_weight;       /* merge-path variant 0, single-matrix plans (and their transposed tile set):
+                               a row end counts as row_weight atoms when the merge path is cut into the
+                               warps' shares, so that a share of many short rows holds fewer items than a
+                               share inside long rows (closing a row costs a warp more than one atom);
+                               the tiles inside a share keep items_per_tile items.  0 or 1 = the paper's
+                               equal rows + atoms; at most 64; batch plans ignore it */
+  int32_t reserved[1];
 } lb_plan_opts_t;
 
 /* What a plan resolved to (for tests, the autotuner and reporting). */
@@ -250,8 +256,8 @@ lb_status_t lb_spmv_noalloc(const int32_t* tile_offsets, int32_t num_tiles, int3
  *
  * Candidate families (bits of lb_tune_opts_t.families; 0 = all):
  *   LB_TUNE_MP_WARP  merge-path, warp workers, items_per_thread 4, 8, 16 with one static unit
- *                    per CTA, items_per_thread 8 with 4 and 8 dynamic units per CTA, and the
- *                    look-back form (variant 3) with items_per_thread 8 and 4
+ *                    per CTA, items_per_thread 4 and 8 with row ends weighted 2 in the shares,
+ *                    and the look-back form (variant 3) with items_per_thread 8 and 4
  *   LB_TUNE_MP_CTA   merge-path, CTA workers: per-thread search (variant 1) and
  *                    bulk-copy ring (variant 2, only for 16-byte aligned buffers),
  *                    items_per_thread 4 and 8
@@ -281,6 +287,7 @@ typedef struct lb_tune_candidate_t {
   int32_t group_size;       /* group-mapped schedules (32 warp-, 256 block-mapped) */
   int32_t mp_variant;       /* merge-path worker variant */
   int32_t units_per_cta;    /* merge-path warp workers: work units per CTA */
+  int32_t row_weight;       /* merge-path variant 0: weight of a row end in the shares (1 = unweighted) */
   float ms;                 /* median time of one lb_spmv in milliseconds (the single time if pruned) */
   float gbps;               /* algorithmic bytes (8 nnz + 4 (rows + 1) + 4 cols + 4 rows) / ms */
   int32_t reps;             /* timed launches */

@@ -64,6 +64,8 @@ def _bind(lib):
     lib.or_merge_split.restype = ctypes.c_int32
     lib.or_merge_splits.argtypes = [ctypes.c_int64, i64p, ctypes.c_int32, ctypes.c_int32, i32p, i32p]
     lib.or_merge_sequence.argtypes = [ctypes.c_int32, ctypes.c_int32, i32p, i8p, i32p]
+    lib.or_weighted_diagonals.argtypes = [ctypes.c_int32, ctypes.c_int32, i32p, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.c_int32, i64p]
     lib.or_row_of_atom.argtypes = [ctypes.c_int32, i32p, i32p]
     lib.or_get_tile.argtypes = [i32p, ctypes.c_int32, ctypes.c_int32]
     lib.or_get_tile.restype = ctypes.c_int32
@@ -188,6 +190,15 @@ class Oracle:
         self.lib.or_merge_sequence(R, N, _p(rp, ctypes.c_int32), _p(kind, ctypes.c_int8), _p(idx, ctypes.c_int32))
         return kind, idx
 
+    def weighted_diagonals(self, rp, w: int, shares: int, items_per_tile: int, tiles_per_share: int):
+        """int64 [shares * (tiles_per_share + 1)]: table diagonals with row ends weighted w."""
+        rp = _c(rp, np.int32)
+        R = rp.shape[0] - 1
+        out = np.empty(shares * (tiles_per_share + 1), dtype=np.int64)
+        self.lib.or_weighted_diagonals(R, int(rp[-1]), _p(rp, ctypes.c_int32), int(w), int(shares),
+                                       int(items_per_tile), int(tiles_per_share), _p(out, ctypes.c_int64))
+        return out
+
     def row_of_atom(self, rp):
         rp = _c(rp, np.int32)
         R = rp.shape[0] - 1
@@ -290,6 +301,10 @@ def merge_sequence(rp):
 
 def row_of_atom(rp):
     return default().row_of_atom(rp)
+
+
+def weighted_diagonals(rp, w, shares, items_per_tile, tiles_per_share):
+    return default().weighted_diagonals(rp, w, shares, items_per_tile, tiles_per_share)
 
 
 def get_tile(prefix, a):

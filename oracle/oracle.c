@@ -138,6 +138,43 @@ void or_merge_sequence(int32_t R, int32_t N, const int32_t* rp, int8_t* kind, in
 }
 
 /*
+ * Table diagonals of a merge path whose worker shares are cut with row ends
+ * weighted w (the library's row_weight option, a cost model for its warp
+ * tiles; the paper's shares are the w = 1 case, Sec. 5.2.1).  The point after
+ * i row ends and j atoms costs w*i + j.  Share c of S runs from the last point
+ * of cost <= floor(c*T/S) to the last point of cost <= floor((c+1)*T/S),
+ * T = w*R + N; its table entry k (k = 0..tpc) is its first diagonal plus
+ * k*ipt, clamped to its last.  The points are found by walking the merged list
+ * from the start, one item at a time.  diag: S*(tpc+1) entries.
+ */
+void or_weighted_diagonals(int32_t R, int32_t N, const int32_t* rp, int32_t w, int32_t S, int32_t ipt, int32_t tpc,
+                           int64_t* diag) {
+  const int64_t T = (int64_t)w * R + N;
+  int64_t* point = (int64_t*)malloc(sizeof(int64_t) * ((size_t)S + 1));
+  /* one walk along the merged list; the bounds c*T/S only grow with c */
+  int32_t i = 0, j = 0;
+  int64_t cost = 0;
+  for (int32_t c = 0; c <= S; ++c) {
+    const int64_t W = (int64_t)c * T / S;
+    while (i < R || j < N) {
+      const int row_end = i < R && (j == N || j >= rp[i + 1]); /* ties: the row end first */
+      const int64_t step = row_end ? w : 1;
+      if (cost + step > W) break;
+      cost += step;
+      if (row_end) ++i;
+      else ++j;
+    }
+    point[c] = (int64_t)i + j;
+  }
+  for (int32_t c = 0; c < S; ++c)
+    for (int32_t k = 0; k <= tpc; ++k) {
+      const int64_t d = point[c] + (int64_t)k * ipt;
+      diag[(int64_t)c * (tpc + 1) + k] = d < point[c + 1] ? d : point[c + 1];
+    }
+  free(point);
+}
+
+/*
  * Tile of every atom (the mapping a schedule's get_tile returns, Sec. 5.2.3):
  * row_of[k] = the row r with rp[r] <= k < rp[r+1], by walking the rows.
  */

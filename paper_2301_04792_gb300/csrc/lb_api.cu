@@ -196,6 +196,10 @@ lb_status_t lb_plan_ex(lb_plan_t* out, const int32_t* tile_offsets, int32_t num_
     set_error("lb_plan: num_cols and ctas_per_sm must be >= 0");
     return LB_ERR_INVALID_ARG;
   }
+  if (o.row_weight < 0 || o.row_weight > 64) {
+    set_error("lb_plan: row_weight must be in [0, 64]");
+    return LB_ERR_INVALID_ARG;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int dev = 0;
   LB_CUDA_TRY(cudaGetDevice(&dev));
@@ -248,7 +252,7 @@ lb_status_t lb_plan_ex(lb_plan_t* out, const int32_t* tile_offsets, int32_t num_
   // schedule, the atom->tile walk used by dvals and lb_atom_tiles.
   lb_status_t st = build_mp_table(p->mp, tile_offsets, num_tiles, num_atoms, o.items_per_thread, o.mp_variant,
                                   p->num_sms, o.ctas_per_sm, nullptr, s, nullptr, nullptr, 0, 0,
-                                  o.units_per_cta, o.tiles_per_share);
+                                  o.units_per_cta, o.tiles_per_share, o.row_weight);
   if (st != LB_OK) return fail(st);
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
@@ -394,7 +398,7 @@ lb_status_t lb_prepare_backward(lb_plan_t p, int32_t num_cols, const int32_t* co
   }
   st = build_mp_table(p->mp_t, p->cp, num_cols, N, p->opts.items_per_thread_t, p->opts.mp_variant, p->num_sms,
                       p->opts.ctas_per_sm, nullptr, s, nullptr, nullptr, 0, 0, p->opts.units_per_cta,
-                      p->opts.tiles_per_share);
+                      p->opts.tiles_per_share, p->opts.row_weight);
   if (st != LB_OK) {
     free_transpose(p);
     return st;

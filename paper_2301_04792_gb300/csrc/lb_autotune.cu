@@ -44,7 +44,8 @@ __global__ void fingerprint_kernel(const int32_t* __restrict__ rp, int32_t R, co
 struct Candidate {
   lb_schedule_t schedule;
   int ipt, group, variant;
-  int units = 1;  // merge-path warp workers: work units per CTA
+  int units = 1;       // merge-path warp workers: work units per CTA
+  int row_weight = 1;  // merge-path variant 0: weight of a row end in the shares
 };
 
 using Key = std::tuple<int, int32_t, int32_t, int32_t, uint64_t, int32_t, int32_t>;
@@ -57,7 +58,7 @@ std::vector<Candidate> candidate_list(lb_schedule_t prior, int families, bool al
   if (prior == LB_THREAD_MAPPED && (families & LB_TUNE_THREAD)) v.push_back({LB_THREAD_MAPPED, 0, 0, 0});
   if (families & LB_TUNE_MP_WARP) {
     for (int ipt : {8, 4, 16}) v.push_back({LB_MERGE_PATH, ipt, 0, 0});
-    for (int units : {4, 8}) v.push_back({LB_MERGE_PATH, 8, 0, 0, units});
+    for (int ipt : {4, 8}) v.push_back({LB_MERGE_PATH, ipt, 0, 0, 1, 2});
     for (int ipt : {8, 4}) v.push_back({LB_MERGE_PATH, ipt, 0, 3});
   }
   if (families & LB_TUNE_MP_CTA) {
@@ -82,6 +83,7 @@ lb_plan_opts_t opts_of(const Candidate& c, int32_t num_cols) {
   o.group_size = c.group;
   o.mp_variant = c.variant;
   o.units_per_cta = c.units;
+  o.row_weight = c.row_weight;
   return o;
 }
 
@@ -237,8 +239,9 @@ lb_status_t lb_autotune(const int32_t* tile_offsets, int32_t num_tiles, int32_t 
       r.group_size = c.group;
       r.mp_variant = c.variant;
       r.units_per_cta = c.units;
+      r.row_weight = c.row_weight;
       if ((c.schedule == prior) && heur < 0 &&
-          (c.schedule != LB_MERGE_PATH || (c.ipt == 8 && c.variant == 0 && c.units == 1)))
+          (c.schedule != LB_MERGE_PATH || (c.ipt == 8 && c.variant == 0 && c.units == 1 && c.row_weight == 1)))
         heur = i;
       if (num_tiles == 0) {
         r.status = LB_OK;

@@ -45,6 +45,7 @@ struct MpTable {
   int workers = 0;       // owners of split-table shares (warps for variant 0, CTAs otherwise), per wave;
                          // for variant 0 workers / 8 work units per wave
   int tiles_per_cta = 0; // tiles per worker
+  int row_weight = 1;    // variant 0: cost of a row end when the shares were cut (1 = rows + atoms)
   int64_t entries = 0;
   int64_t items = 0;
   int32_t num_tiles = 0;
@@ -130,7 +131,7 @@ lb_status_t build_mp_table(MpTable& t, const int32_t* rp, int32_t R, int64_t N, 
                            int ctas_per_sm, const BatchBases* batch, cudaStream_t s,
                            const int64_t* item_prefix = nullptr, const int64_t* row_prefix = nullptr,
                            int num_mats = 0, int wave_items = 0, int units_per_cta = 1,
-                           int tiles_per_share = 1);
+                           int tiles_per_share = 1, int row_weight = 1);
 lb_status_t launch_mp_spmv(const MpTable& t, const SpmvCall& c, cudaStream_t s);
 // dvals[j] = dy[row(j)] * x[idx[j]] (dvals != null) or tile_of_atom[j] = row(j)
 lb_status_t launch_mp_expand(const MpTable& t, const SpmvCall& c, const float* dy, float* dvals,

@@ -294,6 +294,40 @@ __device__ __forceinline__ int2 merge_split(const int32_t* __restrict__ rp, int3
   return make_int2((int)lo, (int)(d - lo));
 }
 
+// Diagonal of the last merge-path point whose cost wr * i + j (i row ends, j
+// atoms) does not exceed W: i is the largest row count with wr * i + rp[i] <= W,
+// and j runs on through row i's atoms as far as W allows.
+__device__ __forceinline__ int64_t weighted_point(const int32_t* __restrict__ rp, int32_t R, int64_t N, int64_t wr,
+                                                  int64_t W) {
+  int64_t lo = 0, hi = R;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (wr * mid + (int64_t)__ldg(rp + mid) <= W) lo = mid;
+    else hi = mid - 1;
+  }
+  const int64_t jmax = lo < R ? (int64_t)__ldg(rp + lo + 1) : N;
+  const int64_t j = W - wr * lo < jmax ? W - wr * lo : jmax;
+  return lo + j;
+}
+
+// Splits of a table with row ends weighted wr in the shares: share c runs
+// between the points of cost floor(c * T / S) and floor((c + 1) * T / S),
+// T = wr * R + N, S = workers; its k-th tile starts k * items_per_tile rows +
+// atoms past the share's first point (clamped to the share's end).
+__global__ void mp_splits_weighted_kernel(const int32_t* __restrict__ rp, int32_t R, int64_t N, int wr, int workers,
+                                          int tpc, int ipt_items, int64_t entries, int2* out, int64_t* diag) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= entries) return;
+  const int64_t c = e / (tpc + 1), k = e % (tpc + 1);
+  const int64_t total = (int64_t)wr * R + N;
+  const int64_t b = weighted_point(rp, R, N, wr, c * total / workers);
+  const int64_t en = weighted_point(rp, R, N, wr, (c + 1) * total / workers);
+  const int64_t d0 = b + k * (int64_t)ipt_items;
+  const int64_t d = d0 < en ? d0 : en;
+  out[e] = merge_split(rp, R, N, d);
+  diag[e] = d;
+}
+
 __global__ void mp_splits_at_kernel(const int32_t* __restrict__ rp, int32_t R, int64_t N,
                                     const int64_t* __restrict__ diag, int64_t entries, int2* out) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -393,8 +427,9 @@ static lb_status_t build_guided_table(MpTable& t, const int32_t* rp, int32_t R, 
 lb_status_t build_mp_table(MpTable& t, const int32_t* rp, int32_t R, int64_t N, int ipt, int variant, int num_sms,
                            int ctas_per_sm, const BatchBases* batch, cudaStream_t s, const int64_t* item_prefix,
                            const int64_t* row_prefix, int num_mats, int wave_items, int units_per_cta,
-                           int tiles_per_share) {
+                           int tiles_per_share, int row_weight) {
   t.release();
+  t.row_weight = 1;
   if (!kernel_tma(ipt, false, false)) {
     set_error("items_per_thread must be 4, 8 or 16");
     return LB_ERR_UNSUPPORTED;
@@ -422,7 +457,12 @@ lb_status_t build_mp_table(MpTable& t, const int32_t* rp, int32_t R, int64_t N, 
     const int64_t max_units = std::max<int64_t>(t.grid, t.items / (32 * kWarps));
     if (units > max_units) units = max_units;
     t.workers = (int)(units * kWarps);
-    const int64_t share = (t.items + t.workers - 1) / t.workers;
+    // row ends weighted in the shares (single-matrix tables of variant 0 only): a share holds at most
+    // its weighted size plus one row end's weight in rows + atoms
+    if (variant == 0 && row_weight > 1 && !(item_prefix && row_prefix && num_mats > 1)) t.row_weight = row_weight;
+    const int64_t share = t.row_weight > 1
+                              ? ((int64_t)t.row_weight * R + N + t.workers - 1) / t.workers + t.row_weight
+                              : (t.items + t.workers - 1) / t.workers;
     int64_t tpc = (share + t.items_per_tile - 1) / t.items_per_tile;
     t.tiles_per_cta = (int)(tpc < 1 ? 1 : tpc);
   } else if (variant == 3) {
@@ -503,6 +543,10 @@ lb_status_t build_mp_table(MpTable& t, const int32_t* rp, int32_t R, int64_t N, 
     cudaStreamSynchronize(s);
     cudaFree(d_begin);
     LB_CUDA_TRY(e);
+  } else if (t.row_weight > 1) {
+    mp_splits_weighted_kernel<<<blocks, threads, 0, s>>>(rp, R, N, t.row_weight, t.workers, t.tiles_per_cta,
+                                                         t.items_per_tile, t.entries, t.splits, t.d_diag);
+    LB_CUDA_TRY(cudaGetLastError());
   } else {
     mp_splits_kernel<<<blocks, threads, 0, s>>>(rp, R, N, t.items, t.workers, t.tiles_per_cta, t.items_per_tile,
                                                 t.entries, t.splits, t.d_diag);

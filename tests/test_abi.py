@@ -106,7 +106,16 @@ def test_autotune_rejects_bad_args_before_any_launch(lib):
     assert b"num_cols" in lib.lb_last_error()
     assert plan.value is None
     assert ctypes.sizeof(_lib.PlanOpts) == 12 * 4
-    assert ctypes.sizeof(_lib.TuneResult) == 5 * 4 + ctypes.sizeof(_lib.PlanOpts) + 20 * 36
+    assert ctypes.sizeof(_lib.TuneResult) == 5 * 4 + ctypes.sizeof(_lib.PlanOpts) + 20 * 40
+
+
+def test_plan_rejects_row_weight_out_of_range_before_any_launch(lib):
+    plan = ctypes.c_void_p()
+    for w in (-1, 65):
+        opts = _lib.PlanOpts(row_weight=w)
+        assert lib.lb_plan_ex(ctypes.byref(plan), None, 0, 0, 3, ctypes.byref(opts), None) == 1
+        assert b"row_weight" in lib.lb_last_error()
+    assert plan.value is None
 
 
 def test_selftest_rejects_unknown_case_without_launching(lib):

@@ -26,7 +26,7 @@ def test_autotune_powerlaw_picks_fastest_and_matches_oracle(lbmod):
     rp, ci, v, xd = to_dev(m.rp, m.ci, m.v, x)
     plan, rep = lbmod.autotune(rp, ci, v, xd, num_cols=m.num_cols, reps=3, use_cache=False)
     cands = rep["candidates"]
-    # merge-path warp x3 static + x2 dynamic units + x2 look-back, CTA x4 (buffers are aligned),
+    # merge-path warp x3 static + x2 row-weighted + x2 look-back, CTA x4 (buffers are aligned),
     # thread-mapped, group-mapped x7
     assert len(cands) == 19
     assert all(c["status"] == 0 for c in cands), cands

@@ -15,6 +15,7 @@ BWD_SCHEDULES = [("thread_mapped", {}), ("warp_mapped", {}), ("block_mapped", {}
                  ("merge_path", {"items_per_thread": 8, "mp_variant": 1}),
                  ("merge_path", {"items_per_thread": 8, "mp_variant": 2}),
                  ("merge_path", {"items_per_thread": 8, "units_per_cta": 8}),
+                 ("merge_path", {"items_per_thread": 4, "row_weight": 3}),
                  ("merge_path", {"items_per_thread": 8, "mp_variant": 3, "tiles_per_share": 2})]
 
 

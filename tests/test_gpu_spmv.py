@@ -27,6 +27,8 @@ SCHEDULES = [("thread_mapped", {}), ("warp_mapped", {}), ("block_mapped", {}),
              ("merge_path", {"items_per_thread": 16, "mp_variant": 2}),
              ("merge_path", {"items_per_thread": 8, "units_per_cta": 4}),
              ("merge_path", {"items_per_thread": 4, "units_per_cta": 16}),
+             ("merge_path", {"items_per_thread": 4, "row_weight": 2}),
+             ("merge_path", {"items_per_thread": 8, "row_weight": 5}),
              ("merge_path", {"items_per_thread": 8, "mp_variant": 3}),
              ("merge_path", {"items_per_thread": 4, "mp_variant": 3, "tiles_per_share": 3}),
              ("merge_path", {"items_per_thread": 16, "mp_variant": 3, "tiles_per_share": 2})]
@@ -115,13 +117,19 @@ def test_unaligned_buffers_take_scalar_path(lbmod):
 
 def test_merge_path_splits_bit_exact(lbmod):
     for name, m in small_cases() + edge_cases():
-        for ipt, var in ((4, 0), (8, 0), (16, 0), (8, 1), (4, 2), (16, 2), (8, 3)):
+        for ipt, var, w in ((4, 0, 1), (8, 0, 1), (16, 0, 1), (8, 1, 1), (4, 2, 1), (16, 2, 1), (8, 3, 1),
+                            (4, 0, 2), (8, 0, 3), (16, 0, 64)):
             rp = to_dev(m.rp)[0]
-            plan = lbmod.Plan(rp, m.nnz, "merge_path", items_per_thread=ipt, mp_variant=var)
+            plan = lbmod.Plan(rp, m.nnz, "merge_path", items_per_thread=ipt, mp_variant=var, row_weight=w)
             diag, ij = plan.splits()
             info = plan.info()
             R, N = m.num_rows, m.nnz
-            if var == 3:
+            if w > 1:
+                # shares cut with row ends weighted w: the oracle's walk along the merged list
+                expect = oracle.weighted_diagonals(m.rp, w, info["num_workers"], info["items_per_tile"],
+                                                   info["tiles_per_cta"])
+                assert np.array_equal(diag, expect), (name, ipt, w)
+            elif var == 3:
                 # guided shares: tiles of items_per_tile items in order, each share ending where
                 # the next begins, the last at R + N
                 assert diag[0] == 0 and diag[-1] == R + N and (np.diff(diag) >= 0).all()

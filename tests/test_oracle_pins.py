@@ -147,6 +147,36 @@ def test_merge_path_matches_bruteforce_merge():
     check_merge(oracle.default())
 
 
+def check_weighted_diagonals(orc):
+    """Shares cut with row ends weighted w: against the brute-force merged list
+    (cost of every prefix by a cumulative sum, last prefix within each share's
+    bound by a search), against the unweighted layout written out for w = 1,
+    and the size bound a table relies on."""
+    for t, (C, rp, ci, v) in enumerate(tiny_cases(5)):
+        seq = brute_merge(rp)
+        R, N = len(rp) - 1, int(rp[-1])
+        for w in (1, 2, 3, 7):
+            cost = np.concatenate([[0], np.cumsum([w if kind == 0 else 1 for kind, _ in seq])]).astype(np.int64)
+            T = w * R + N
+            for S, ipt in ((1, 4), (3, 2), (5, 3), (16, 1)):
+                tpc = (-(-T // S) + w + ipt - 1) // ipt
+                d = orc.weighted_diagonals(rp, w, S, ipt, tpc).reshape(S, tpc + 1)
+                bounds = np.arange(S + 1, dtype=np.int64) * T // S
+                pts = np.searchsorted(cost, bounds, side="right") - 1   # last prefix of cost <= bound
+                assert np.array_equal(d[:, 0], pts[:-1]) and np.array_equal(d[:, -1], pts[1:]), (t, w, S)
+                for c in range(S):
+                    expect = np.minimum(pts[c] + np.arange(tpc + 1) * ipt, pts[c + 1])
+                    assert np.array_equal(d[c], expect), (t, w, S, c)
+                assert (pts[1:] - pts[:-1] <= tpc * ipt).all()            # every share fits its tiles
+                if w == 1:
+                    assert np.array_equal(pts, bounds)                    # the equal rows + atoms shares
+                assert pts[0] == 0 and pts[-1] == R + N
+
+
+def test_weighted_shares_match_bruteforce():
+    check_weighted_diagonals(oracle.default())
+
+
 def test_merge_path_split_invariants_and_coverage():
     rng = np.random.default_rng(11)
     import workloads as W
@@ -419,6 +449,8 @@ MUTANTS = {
     "merge_ties_to_atoms": ("if ((int64_t)rp[mid + 1] > d - mid - 1) hi = mid;",
                             "if ((int64_t)rp[mid + 1] >= d - mid - 1) hi = mid;", check_merge),
     "sequence_ties_to_atoms": ("(j >= N || rp[i + 1] <= j)", "(j >= N || rp[i + 1] < j)", check_merge),
+    # weighted shares that stop one item short (a point whose cost equals the bound left out)
+    "weighted_share_short": ("if (cost + step > W) break;", "if (cost + step >= W) break;", check_weighted_diagonals),
     # unstable transpose: rows visited bottom-up
     "unstable_transpose": ("for (int32_t r = 0; r < R; ++r) {\n    for (int32_t k = rp[r]; k < rp[r + 1]; ++k) {\n"
                            "      int32_t p = cur",
