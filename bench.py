@@ -677,31 +677,47 @@ def run_ours(args, ws, rank, local):
     h_ci = torch.from_numpy(m.ci).pin_memory()
     h_v = torch.from_numpy(m.v).pin_memory()
     h_x = torch.from_numpy(x_np).pin_memory()
-    h_y = torch.empty(R, dtype=torch.float32).pin_memory()
+    h_y = [torch.empty(R, dtype=torch.float32).pin_memory() for _ in range(2)]
     e2e_plan = plans[0]
     h2d = h_rp.numel() * 4 + h_ci.numel() * 4 + h_v.numel() * 4 + h_x.numel() * 4
     d2h = R * 4
+    # two streams, each with its own plan and device copy of the inputs: step k+1's host-to-device
+    # copies run while step k's SpMV and its result copy do (a serving loop); a stream's next step
+    # reuses its buffers only after its previous step's copy-out (stream order)
+    e2e_streams = [torch.cuda.Stream(device=device) for _ in range(2)]
+    x_e = [x_d, torch.empty_like(x_d)]
 
-    def e2e_step():
-        rp_d[0].copy_(h_rp, non_blocking=True)
-        ci_d[0].copy_(h_ci, non_blocking=True)
-        v_d[0].copy_(h_v, non_blocking=True)
-        x_d.copy_(h_x, non_blocking=True)
-        e2e_plan.spmv(ci_d[0], v_d[0], x_d, y_d[0])
-        h_y.copy_(y_d[0], non_blocking=True)
+    def e2e_step(k):
+        b = k % 2
+        st = e2e_streams[b]
+        with torch.cuda.stream(st):
+            rp_d[b].copy_(h_rp, non_blocking=True)
+            ci_d[b].copy_(h_ci, non_blocking=True)
+            v_d[b].copy_(h_v, non_blocking=True)
+            x_e[b].copy_(h_x, non_blocking=True)
+            plans[b].spmv(ci_d[b], v_d[b], x_e[b], y_d[b], stream=st.cuda_stream)
+            h_y[b].copy_(y_d[b], non_blocking=True)
 
-    for _ in range(0 if args.ncu else 3):
-        e2e_step()
+    for st in e2e_streams:
+        st.wait_stream(stream)
+    for k in range(0 if args.ncu else 4):
+        e2e_step(k)
     torch.cuda.synchronize()
     barrier(ws)
-    k_e2e = 1 if args.ncu else max(3, min(args.steps, 50))
+    k_e2e = 2 if args.ncu else max(4, min(args.steps, 50))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(k_e2e):
-        e2e_step()
+    for st in e2e_streams:
+        st.wait_stream(stream)
+    for k in range(k_e2e):
+        e2e_step(k)
+    for st in e2e_streams:
+        stream.wait_stream(st)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / k_e2e, ws, device)
+    h_y = h_y[(k_e2e - 1) % 2]  # the last step's result, read back inside the timed region
+    e2e_ok = bool((np.abs(h_y.numpy()[sample].astype(np.float64) - y64) <= oracle.TOL * bnd).all())
     e2e_val = ws * byts / (e2e_ms * 1e-3) / 1e9
 
     # zero copy: the kernel streams col_idx / vals straight from pinned host memory over the
@@ -728,8 +744,6 @@ def run_ours(args, ws, rank, local):
               "h2d_bytes_per_step": h_ci.numel() * 4 + h_v.numel() * 4 + h_x.numel() * 4,
               "d2h_bytes_per_step": R * 4, "ok": zc_ok,
               "note": "lb_spmv reads col_idx/vals from pinned host memory (zero copy); host link ~210 GB/s"}
-    e2e_ok = bool(np.allclose(h_y.numpy()[sample].astype(np.float64), y64, atol=0, rtol=0) or
-                  (np.abs(h_y.numpy()[sample].astype(np.float64) - y64) <= oracle.TOL * bnd).all())
 
     # SpMM C = A B (Listing 4) on the same matrix, B dense [cols, K]
     spmm = None
@@ -825,7 +839,8 @@ def run_ours(args, ws, rank, local):
             "configs": configs,
             "schedules_GBps": sched,
             "e2e": {"value": round(e2e_val, 2), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "ms_per_step": round(e2e_ms, 4), "ok": e2e_ok},
+                    "ms_per_step": round(e2e_ms, 4), "ok": e2e_ok,
+                    "note": "two streams: step k+1's copies in overlap step k's SpMV and copy out"},
             "e2e_zero_copy": zc,
             "gpu_launches": args.steps * info["kernels_per_spmv"],
             "clocks": clocks,
