@@ -432,7 +432,9 @@ lb_schedule_t lb_heuristic_schedule(int32_t rows, int32_t cols, int64_t nnz);
  * tiles of items_per_tile; entry c*(tiles_per_cta+1)+k is
  * min(share_begin(c) + k*items_per_tile, share_end(c)), with
  * tiles_per_cta = ceil(max share / items_per_tile).  Writes min(count, cap)
- * diagonals to host_diag and the total count to *count.
+ * diagonals to host_diag and the total count to *count.  This is the layout
+ * of plans with row_weight 0 or 1; the shares of a weighted plan depend on
+ * the row offsets (lb_plan_splits returns them).
  */
 lb_status_t lb_merge_diagonals(int64_t items, int32_t grid, int32_t items_per_tile, int64_t* host_diag, size_t cap,
                                size_t* count, int32_t* tiles_per_cta);
