@@ -886,7 +886,11 @@ struct WarpSplits {
 // every atom is loaded on its own.  ONE_ROW: a tile inside a single row is
 // summed without the row pass and the segmented scan (the look-back kernel,
 // whose guided shares gain from it; the static kernel measured faster without).
-template <int IPT, bool XB, bool PERM, bool VEC, bool ONE_ROW = false>
+// SPLIT_CHECK: whether the launch validates column indices is tested once per
+// tile (the same answer for every warp), so an unvalidated launch gathers
+// without a test per atom (the look-back kernel: the stencil 285 -> 261 us;
+// the static kernel measured slower in that form and keeps the per-atom one).
+template <int IPT, bool XB, bool PERM, bool VEC, bool ONE_ROW = false, bool SPLIT_CHECK = false>
 struct WarpWalker {
   static_assert(IPT % 4 == 0 && 32 % IPT == 0, "IPT must be 4, 8 or 16");
   const MpArgs& a;
@@ -940,6 +944,19 @@ struct WarpWalker {
       m0 = __ldg(sm);
       m1 = __ldg(sm + 1);
       xb0 = __ldg(a.vec_base + m0);
+    }
+    if (SPLIT_CHECK && a.atoms.check <= 0) {
+#pragma unroll
+      for (int q = 0; q < IPT; ++q) {
+        const int l = s0 + q - off;
+        xg[q] = 0.f;
+        vv[q] = 0.f;
+        if ((unsigned)l < (unsigned)nnz) {
+          xg[q] = __ldg(a.atoms.vec + atom_xbase<XB>(a, m0, m1, xb0, (int64_t)j0 + l) + c[q]);
+          vv[q] = PERM ? __ldg(a.atoms.val + vb[q]) : __int_as_float(vb[q]);
+        }
+      }
+      return;
     }
 #pragma unroll
     for (int q = 0; q < IPT; ++q) {
@@ -1195,7 +1212,7 @@ __global__ void __launch_bounds__(256, IPT <= 8 ? 4 : 2) mp_spmv_lookback_kernel
   __shared__ int s_pend[WPB][32];  // shares whose first row waits for its predecessors' sums
   __shared__ int s_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  WarpWalker<IPT, XB, PERM, VEC, true> wk(a, sc_all[warp]);
+  WarpWalker<IPT, XB, PERM, VEC, true, true> wk(a, sc_all[warp]);
   const unsigned epoch = *reinterpret_cast<volatile unsigned*>(a.ticket + 2);
   auto add_to_first_row = [&](int p, float total) {
     float* py = a.out + __ldg(&a.share_head[p].x);
