@@ -118,6 +118,17 @@ def test_plan_rejects_row_weight_out_of_range_before_any_launch(lib):
     assert plan.value is None
 
 
+def test_candidate_names_carry_units_and_row_weight():
+    from paper_2301_04792_gb300 import lb as lbm
+    c = _lib.TuneCandidate(schedule=3, items_per_thread=4, mp_variant=0, units_per_cta=1, row_weight=2)
+    assert lbm._candidate_name(c) == "merge_path_ipt4_v0_w2"
+    c = _lib.TuneCandidate(schedule=3, items_per_thread=8, mp_variant=0, units_per_cta=4, row_weight=1)
+    assert lbm._candidate_name(c) == "merge_path_ipt8_v0_u4"
+    c = _lib.TuneCandidate(schedule=3, items_per_thread=8, mp_variant=3, units_per_cta=1, row_weight=0)
+    assert lbm._candidate_name(c) == "merge_path_ipt8_v3"
+    assert ctypes.sizeof(_lib.TuneCandidate) == 10 * 4
+
+
 def test_selftest_rejects_unknown_case_without_launching(lib):
     assert lib.lb_selftest(0, None) == 1
     assert lib.lb_selftest(3, None) == 1
