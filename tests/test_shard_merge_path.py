@@ -3,7 +3,8 @@ CPU with gloo, world sizes 2 and 3): rank r owns the r-th equal share of rows + 
 split on its diagonals by the oracle's merge-path search; it sums the atoms of its
 share into the rows they belong to, the boundary rows' partial sums meet in one
 all-reduce, and the result equals the full SpMV exactly (integer-valued inputs make
-every FP64 sum exact)."""
+every FP64 sum exact).  The same holds when the shares are cut with row ends weighted
+(the row_weight cut: equal cost w * rows + atoms per rank)."""
 import os
 import socket
 
@@ -28,7 +29,7 @@ def _case():
     return m, v, x
 
 
-def _worker(rank, world, port, out):
+def _worker(rank, world, port, out, w=1):
     import torch
     import torch.distributed as dist
     import oracle
@@ -37,7 +38,12 @@ def _worker(rank, world, port, out):
     m, v, x = _case()
     R, N = m.num_rows, m.nnz
     items = R + N
-    d0, d1 = rank * items // world, (rank + 1) * items // world
+    if w == 1:
+        d0, d1 = rank * items // world, (rank + 1) * items // world
+    else:
+        # start and end diagonal of each rank's weighted share (one tile spanning the whole share)
+        diag = oracle.weighted_diagonals(m.rp, w, world, w * R + N + 1, 1).reshape(world, 2)
+        d0, d1 = int(diag[rank, 0]), int(diag[rank, 1])
     (i0, j0), (i1, j1) = oracle.merge_split(d0, m.rp), oracle.merge_split(d1, m.rp)
     # this rank's atoms [j0, j1) summed into their rows (the boundary rows partly)
     y = np.zeros(R, dtype=np.float64)
@@ -51,12 +57,12 @@ def _worker(rank, world, port, out):
     dist.destroy_process_group()
 
 
-def _run(world):
+def _run(world, w=1):
     ctx = mp.get_context("spawn")
     port = _free_port()
     with ctx.Manager() as man:
         out = man.dict()
-        procs = [ctx.Process(target=_worker, args=(r, world, port, out)) for r in range(world)]
+        procs = [ctx.Process(target=_worker, args=(r, world, port, out, w)) for r in range(world)]
         for p in procs:
             p.start()
         for p in procs:
@@ -66,8 +72,8 @@ def _run(world):
 
 
 def test_merge_path_shards_sum_to_the_full_spmv():
-    for world in (2, 3):
-        res = _run(world)
+    for world, w in ((2, 1), (3, 1), (3, 4)):
+        res = _run(world, w)
         assert all(ok for ok, *_ in res)
         # the shards tile the merge path: each starts where the previous ended
         for (_, _, _, i1, j1), (_, i0, j0, _, _) in zip(res, res[1:]):
