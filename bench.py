@@ -233,6 +233,27 @@ def run_reference(args, ws, rank):
 
 # ------------------------------------------------------------------ GPU side --
 
+def all_within(oracle, items, threads, grads=None):
+    """True when every (matrix, x, y32) has y32 within the oracle's bound on every row; with
+    grads = [(dy, dx32, dvals32)] per item, dx within the bound and dvals bit-exact too.  The
+    oracle runs per matrix on a thread pool (its C loops release the GIL)."""
+    import concurrent.futures as cf
+
+    def one(k):
+        m, x, y32 = items[k]
+        y64, b = oracle.spmv(m.rp, m.ci, m.v, x)
+        if not oracle.within_bound(y32, y64, b).all():
+            return False
+        if grads is None:
+            return True
+        dy, dx32, dv32 = grads[k]
+        dx64, bx, dv = oracle.grad(m.rp, m.ci, m.v, x, dy, m.num_cols)
+        return bool(oracle.within_bound(dx32, dx64, bx).all()) and np.array_equal(dv.view(np.uint32),
+                                                                           dv32.view(np.uint32))
+    with cf.ThreadPoolExecutor(max_workers=max(1, threads)) as ex:
+        return all(ex.map(one, range(len(items))))
+
+
 def time_launches(torch, launch, n, stream):
     """Per-launch durations (ms) from CUDA events recorded on the launching stream."""
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
@@ -312,7 +333,8 @@ def bench_configs(torch, lb, W, device, peak, cores):
     rp_cat = torch.from_numpy(b.rp_cat()).to(device)
     ci = torch.from_numpy(b.ci_cat()).to(device)
     v = torch.from_numpy(b.v_cat()).to(device)
-    x = torch.rand(int(cols.sum()), device=device)
+    xs = [W.x_for(m, seed=i) for i, m in enumerate(b.mats)]
+    x = torch.from_numpy(np.concatenate(xs)).to(device)
     y = torch.empty(int(rows.sum()), device=device)
     bp = lb.BatchPlan(rows, cols, nnz, rp_cat, mp_variant=3, items_per_thread=4)
     rb = np.concatenate([[0], np.cumsum(rows)])
@@ -358,7 +380,13 @@ def bench_configs(torch, lb, W, device, peak, cores):
             ts.append(e0.elapsed_time(e1))
         return statistics.median(ts)
     t_b = timed(g.replay)
+    # parity of the timed batched launch: every row against the oracle
+    g.replay()
+    y_b = y.cpu().numpy()
+    ok_b = all_within(oracle, [(m, xs[i], y_b[rb[i]:rb[i + 1]]) for i, m in enumerate(b.mats)], cores)
     t_p = timed(lambda: per_matrix(torch.cuda.current_stream(device).cuda_stream))
+    y_p = y.cpu().numpy()
+    ok_p = all_within(oracle, [(m, xs[i], y_p[rb[i]:rb[i + 1]]) for i, m in enumerate(b.mats)], cores)
     t_pg = timed(gp.replay)
     R, C, N = int(rows.sum()), int(cols.sum()), int(nnz.sum())
     byts = 8 * N + 4 * (R + b.num) + 4 * C + 4 * R
@@ -368,7 +396,8 @@ def bench_configs(torch, lb, W, device, peak, cores):
                        "speedup_vs_graph": round(t_pg / t_b, 3), "GBps": round(gbps, 2),
                        "frac_of_8TBps": round(gbps / 8000.0, 4), "frac_of_measured": round(gbps / peak, 4),
                        "GFLOPs": round(2 * N / (t_b * 1e-3) / 1e9, 2),
-                       "batch_plan": "merge_path_ipt4_v3", "per_matrix_plan": "merge_path_ipt8_v0 (library default)"}
+                       "batch_plan": "merge_path_ipt4_v3", "per_matrix_plan": "merge_path_ipt8_v0 (library default)",
+                       "parity_all_rows": {"batched": ok_b, "per_matrix": ok_p}}
     for p in plans:
         p.close()
     bp.close()
@@ -377,7 +406,7 @@ def bench_configs(torch, lb, W, device, peak, cores):
     return out
 
 
-def bench_batched(torch, lb, W, device, reps=5):
+def bench_batched(torch, lb, W, device, cores=1, reps=5):
     """Per-matrix fwd+bwd launches vs. batched persistent launches replayed from a CUDA graph."""
     b = W.diff_batch()
     rows, cols, nnz = b.rows(), b.cols(), b.nnz()
@@ -388,7 +417,6 @@ def bench_batched(torch, lb, W, device, reps=5):
     v = torch.from_numpy(b.v_cat()).to(device)
     x = torch.from_numpy(np.concatenate(xs)).to(device)
     dy = torch.from_numpy(np.concatenate(dys)).to(device)
-    del xs, dys
     R, C, N = int(rows.sum()), int(cols.sum()), int(nnz.sum())
     y = torch.empty(R, device=device)
     dx = torch.empty(C, device=device)
@@ -471,10 +499,22 @@ def bench_batched(torch, lb, W, device, reps=5):
         return statistics.median(ts)
 
     t_batch = timed(g.replay)
+    import oracle
+
+    def parity():
+        # y, dx and dvals of every matrix from the last pass against the oracle
+        yh, dxh, dvh = y.cpu().numpy(), dx.cpu().numpy(), dv.cpu().numpy()
+        items = [(m, xs[i], yh[rb[i]:rb[i + 1]]) for i, m in enumerate(b.mats)]
+        grads = [(dys[i], dxh[cb[i]:cb[i + 1]], dvh[nb[i]:nb[i + 1]]) for i in range(b.num)]
+        return all_within(oracle, items, cores, grads)
+    g.replay()
+    ok_batch = parity()
     t_plains = {k: timed(r(torch.cuda.current_stream(device).cuda_stream)) for k, (_, _, r) in plains.items()}
     best = min(t_plains, key=t_plains.get)
     t_plain = t_plains[best]
     _, calls_list, runner = plains[best]
+    runner(torch.cuda.current_stream(device).cuda_stream)()
+    ok_plain = parity()
     # the faster per-matrix configuration's launches captured in a graph too (no host launch cost)
     gp = torch.cuda.CUDAGraph()
     cap = torch.cuda.Stream(device=device)
@@ -508,6 +548,8 @@ def bench_batched(torch, lb, W, device, reps=5):
            "speedup": round(t_plain / t_batch, 4), "plain_graph_ms": round(t_plain_graph, 4),
            "speedup_vs_plain_graph": round(t_plain_graph / t_batch, 4),
            "plain_launches": 3 * b.num, "batched_launches": 3, "parts": parts,
+           "parity_all_matrices": {"batched": ok_batch, "per_matrix": ok_plain,
+                                   "checked": "y and dx of every row / column within the bound, dvals bit-exact"},
            "fwd_bwd_bytes": byts, "batched_GBps": round(byts / (t_batch * 1e-3) / 1e9, 2),
            "plain_GBps": round(byts / (t_plain * 1e-3) / 1e9, 2)}
     for plans_k, _, _ in plains.values():
@@ -772,7 +814,7 @@ def run_ours(args, ws, rank, local):
 
     batched = None
     if not args.no_batch and not args.ncu:
-        batched = bench_batched(torch, lb, W, device)
+        batched = bench_batched(torch, lb, W, device, host_cores())
 
     configs = None
     if not args.quick and not args.ncu and not args.no_batch:
@@ -854,7 +896,7 @@ def run_ours(args, ws, rank, local):
 
 
 PROFILE_CASES = ("lookback_rmat", "lookback_stencil", "thread_mapped_powerlaw", "block_mapped_powerlaw", "spmm_k32_powerlaw",
-                 "sssp_rmat", "batch_fwd_bwd_diff4")
+                 "sssp_rmat", "batch_fwd_bwd_diff4", "gather_probe_powerlaw")
 
 
 def run_case(name: str):
@@ -868,7 +910,21 @@ def run_case(name: str):
     def d(*arrays):
         return [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in arrays]
 
-    if name == "sssp_rmat":
+    if name == "gather_probe_powerlaw":
+        # the gather-ceiling probe (stream col_idx / vals, gather x, nothing else) on the power-law matrix
+        import ctypes
+        from paper_2301_04792_gb300 import _lib
+        lib = _lib.load()
+        m = W.powerlaw()
+        ci, v, x = d(m.ci, m.v, W.x_for(m))
+        grid = lib.lb_probe_gather_grid()
+        out = torch.empty(grid * 256, device=dev)
+        vp = ctypes.c_void_p
+        for _ in range(3):
+            _lib.check(lib.lb_probe_gather(vp(ci.data_ptr()), vp(v.data_ptr()), vp(x.data_ptr()), m.nnz - m.nnz % 4,
+                                           vp(out.data_ptr()), grid, vp(torch.cuda.current_stream().cuda_stream)),
+                       "lb_probe_gather")
+    elif name == "sssp_rmat":
         g = W.rmat()
         rp, ci, w = d(g.rp, g.ci, g.v.astype(np.float32))
         lb.sssp(rp, ci, w, 0, group_size=256)

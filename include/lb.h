@@ -223,24 +223,28 @@ lb_status_t lb_status(lb_plan_t plan, void* stream);
 /*
  * y = A x by the merge-path schedule without a plan and without allocating any
  * device memory (the paper has no counterpart: it is a convenience of this
- * library).  For callers that cannot call cudaMalloc: code that runs while a
- * CUDA graph is being captured, allocator-free real-time or embedded loops that
- * reserve all device memory up front, and hosts whose memory pool does not
- * let a library take blocks of its own.  Arguments are those of lb_plan plus
- * lb_spmv (tile_offsets, col_idx, vals, x, y: device pointers, caller-owned,
- * same layouts); y is overwritten.
+ * library).  For callers that cannot call cudaMalloc: allocator-free
+ * real-time or embedded loops that reserve all device memory up front
+ * (cudaMalloc may synchronise the device and take unbounded time), and hosts
+ * whose memory pool is owned by another framework that does not let a library
+ * take blocks of its own.  Arguments are those of lb_plan plus lb_spmv
+ * (tile_offsets, col_idx, vals, x, y: device pointers, caller-owned, same
+ * layouts); y is overwritten.  Column indices are NOT checked: every col_idx
+ * entry must lie in [0, length of x), or the kernel reads outside x; for
+ * untrusted input use lb_plan_ex with validation and lb_spmv.
  * Scratch: the split table, carry slots and fix-up ticket live in one fixed
  * 8 MiB device array compiled into the library, which every GPU that loads the
  * library holds until the process exits.  A problem whose scratch would not fit
- * (on a 152-SM GB300 about 130 million rows + nonzeros) is rejected with
+ * (on a 152-SM GB300 about 260 million rows + nonzeros) is rejected with
  * LB_ERR_UNSUPPORTED before anything is launched; use lb_plan + lb_spmv then.
- * The first call on a device looks up the array's device address (and the
- * kernel's occupancy) with that device current; make that first call before
+ * The first call on a device looks up the array's device address, the kernels
+ * and their occupancy with that device current; make that first call before
  * any stream capture.  Every call on a device shares the array and the array
- * keeps the previous call's contents, so calls that overlap on the GPU (other
- * streams, other threads) race: serialise them.  Launches two kernels on
- * `stream`, no synchronisation.  Errors: LB_ERR_INVALID_ARG (negative sizes,
- * NULL buffers), LB_ERR_UNSUPPORTED (too large), LB_ERR_CUDA.
+ * keeps the previous call's contents (the ticket is cleared by each call), so
+ * calls that overlap on the GPU (other streams, other threads) race: serialise
+ * them.  Launches two kernels and one 8-byte memset on `stream`, no
+ * synchronisation.  Errors: LB_ERR_INVALID_ARG (negative sizes, NULL
+ * buffers), LB_ERR_UNSUPPORTED (too large), LB_ERR_CUDA.
  */
 lb_status_t lb_spmv_noalloc(const int32_t* tile_offsets, int32_t num_tiles, int32_t num_atoms,
                             const int32_t* col_idx, const float* vals, const float* x, float* y, void* stream);

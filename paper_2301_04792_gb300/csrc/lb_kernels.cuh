@@ -621,9 +621,13 @@ __global__ void __launch_bounds__(BLOCK) mp_spmv_tma_kernel(MpArgs a) {
     if (s_abort) break;
   }
   if (s_abort && tid == 0) {
-    // wind down: wait (bounded) for this CTA's bulk copies still in flight
+    // wind down: wait for this CTA's bulk copies still in flight, each with four
+    // times the normal bound, so that no copy lands in shared memory after the
+    // CTA has left.  The copies read in-bounds global ranges taken from the
+    // plan's split table, so they complete; one that outlasts both bounds means
+    // the device has stopped making progress altogether
     for (int t = waited > 0 ? waited - 1 : 0; t < issued; ++t)
-      mbar_wait_bounded(&s_bar[t % kStages], (uint32_t)((t / kStages) & 1));
+      mbar_wait_bounded(&s_bar[t % kStages], (uint32_t)((t / kStages) & 1), 4 * kSpinLimit);
   }
   if (!publish_carry<BLOCK>(a, open_row, carry, &s_last)) return;
   last_cta_fixup<BLOCK>(a, a.num_ctas, s_wv, s_wf, s_incl);

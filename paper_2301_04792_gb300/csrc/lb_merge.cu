@@ -234,7 +234,7 @@ __global__ void mp_splits_kernel(const int32_t* __restrict__ rp, int32_t R, int6
     else lo = mid + 1;
   }
   out[e] = make_int2((int)lo, (int)(d - lo));
-  diag[e] = d;
+  if (diag) diag[e] = d;
 }
 
 // Splits of a waved table: entry e belongs to wave v (largest v with

@@ -1,13 +1,14 @@
 // Merge-path SpMV for callers that cannot allocate device memory.
 //
-// Some callers must not call cudaMalloc at all: code running while a CUDA
-// graph is being captured, allocator-free embedded or real-time loops that
-// budget all device memory up front, and hosts whose memory pool forbids a
-// library from reserving its own blocks.  lb_spmv_noalloc serves them: it
-// needs no plan object and allocates nothing.  Its scratch (the merge-path
-// split table, one carry slot per warp worker and the fix-up ticket) lives in
-// the fixed file-scope device array below, which every GPU that loads this
-// library holds until the process exits.
+// Some callers must not call cudaMalloc at all: allocator-free embedded or
+// real-time loops that reserve all device memory up front (cudaMalloc may
+// synchronise the device and take unbounded time), and hosts whose memory
+// pool is owned by another framework and forbids a library from reserving its
+// own blocks.  lb_spmv_noalloc serves them: it needs no plan object and
+// allocates nothing.  Its scratch (the merge-path split table, one carry slot
+// per warp worker and the fix-up ticket) lives in the fixed file-scope device
+// array below, which every GPU that loads this library holds until the
+// process exits.
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -56,8 +57,12 @@ lb_status_t setup_device(int dev, DeviceSetup** out) {
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lbk::mp_spmv_warp_kernel<kIpt, false, false, true>,
                                                       kBlock, 0);
+    // load every kernel the entry point launches now, not at its first launch
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, lbk::mp_spmv_warp_kernel<kIpt, false, false, false>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, mp_splits_kernel);
     if (e != cudaSuccess) {
-      set_error(std::string("lb_spmv_noalloc: occupancy query failed: ") + cudaGetErrorString(e));
+      set_error(std::string("lb_spmv_noalloc: kernel set-up failed: ") + cudaGetErrorString(e));
       return LB_ERR_CUDA;
     }
     d.base = static_cast<unsigned char*>(ptr);
@@ -108,12 +113,11 @@ lb_status_t lb_spmv_noalloc(const int32_t* tile_offsets, int32_t num_tiles, int3
   if (tpc < 1) tpc = 1;
   const int64_t entries = workers * (tpc + 1);
 
-  // scratch layout: ticket | carry rows | carry values | splits | diagonals
+  // scratch layout: ticket | carry rows | carry values | splits (the diagonals are not kept)
   const size_t off_rows = 256;
   const size_t off_vals = round_up(off_rows + sizeof(int32_t) * (size_t)workers, 256);
   const size_t off_splits = round_up(off_vals + sizeof(float) * (size_t)workers, 256);
-  const size_t off_diag = round_up(off_splits + sizeof(int2) * (size_t)entries, 256);
-  const size_t need = off_diag + sizeof(int64_t) * (size_t)entries;
+  const size_t need = off_splits + sizeof(int2) * (size_t)entries;
   if (need > kNoAllocBytes) {
     set_error("lb_spmv_noalloc: problem needs " + std::to_string(need) + " bytes of scratch, more than the " +
               std::to_string(kNoAllocBytes) + " the no-allocation entry point has (use lb_plan + lb_spmv)");
@@ -124,10 +128,9 @@ lb_status_t lb_spmv_noalloc(const int32_t* tile_offsets, int32_t num_tiles, int3
   // the ticket and unit counter must start at zero; the array keeps the previous call's contents
   LB_CUDA_TRY(cudaMemsetAsync(base, 0, 2 * sizeof(unsigned), s));
   int2* splits = reinterpret_cast<int2*>(base + off_splits);
-  int64_t* diag = reinterpret_cast<int64_t*>(base + off_diag);
   const unsigned sblocks = (unsigned)((entries + 255) / 256);
   mp_splits_kernel<<<sblocks, 256, 0, s>>>(tile_offsets, num_tiles, num_atoms, items, (int)workers, (int)tpc,
-                                           items_per_tile, entries, splits, diag);
+                                           items_per_tile, entries, splits, nullptr);
   LB_CUDA_TRY(cudaGetLastError());
 
   lbk::MpArgs a{};

@@ -130,40 +130,61 @@ def test_batched_graph_replay(lbmod):
     assert_within_bound(dx.cpu().numpy(), dx64, dxb, "graph dx")
 
 
+# the configuration bench.py times for both batched workloads (look-back shares, items_per_thread 4)
+BENCHED = dict(mp_variant=3, items_per_thread=4)
+
+
 def test_full_batch_512(lbmod):
-    """The 512-matrix batch at full size: forward on every row."""
+    """The 512-matrix batch at full size: forward on every row, for the library's
+    default batch plan and for the plan the bench times; repeated runs bit-identical."""
     import torch
     b = W.batch()
     xs = [W.x_for(m, seed=i) for i, m in enumerate(b.mats)]
-    y64 = np.concatenate([oracle.spmv(m.rp, m.ci, m.v, x)[0] for m, x in zip(b.mats, xs)])
-    yb = np.concatenate([oracle.spmv(m.rp, m.ci, m.v, x)[1] for m, x in zip(b.mats, xs)])
-    plan, rp_cat, ci, v = make_plan(lbmod, b)
+    ref = [oracle.spmv(m.rp, m.ci, m.v, x) for m, x in zip(b.mats, xs)]
+    y64 = np.concatenate([r[0] for r in ref])
+    yb = np.concatenate([r[1] for r in ref])
     xd = to_dev(np.concatenate(xs))[0]
-    y = plan.spmv(ci, v, xd)
-    y2 = plan.spmv(ci, v, xd)
-    assert_within_bound(y.cpu().numpy(), y64, yb, "batch512 y")
-    assert torch.equal(y.view(torch.int32), y2.view(torch.int32))
+    for kw in ({}, BENCHED):
+        plan, rp_cat, ci, v = make_plan(lbmod, b, **kw)
+        y = plan.spmv(ci, v, xd)
+        y2 = plan.spmv(ci, v, xd)
+        assert_within_bound(y.cpu().numpy(), y64, yb, f"batch512 y {kw}")
+        assert torch.equal(y.view(torch.int32), y2.view(torch.int32))
+        plan.close()
+        del rp_cat, ci, v
 
 
 def test_full_differentiable_batch_64(lbmod):
-    """64 power-law matrices of 2^20 rows (~16M nnz each): fwd + bwd on sampled matrices' rows
-    and columns, dvals bit-exact on sampled atoms."""
+    """64 power-law matrices of 2^20 rows (~16M nnz each): y, dx and dvals of
+    every matrix against the oracle (y and dx within the bound, dvals bit-exact),
+    for the default batch plan and for the plan the bench times; a second pass
+    bit-identical."""
     import torch
     b = W.diff_batch()
     xs, dys = batch_inputs(b)
-    plan, rp_cat, ci, v = make_plan(lbmod, b)
     xd, dyd = to_dev(np.concatenate(xs), np.concatenate(dys))
-    y = plan.spmv(ci, v, xd).cpu().numpy()
-    dx, dvals = plan.backward(ci, v, xd, dyd)
-    dx, dvals = dx.cpu().numpy(), dvals.cpu().numpy()
     rows, cols, nnz = b.rows(), b.cols(), b.nnz()
     rb = np.concatenate([[0], np.cumsum(rows)])
     cb = np.concatenate([[0], np.cumsum(cols)])
     nb = np.concatenate([[0], np.cumsum(nnz)])
-    for mi in (0, 17, 63):
-        m = b.mats[mi]
+    results = {}
+    for name, kw in (("default", {}), ("benched", BENCHED)):
+        plan, rp_cat, ci, v = make_plan(lbmod, b, **kw)
+        y = plan.spmv(ci, v, xd)
+        dx, dvals = plan.backward(ci, v, xd, dyd)
+        y2 = plan.spmv(ci, v, xd)
+        dx2, dvals2 = plan.backward(ci, v, xd, dyd)
+        assert torch.equal(y.view(torch.int32), y2.view(torch.int32)), name
+        assert torch.equal(dx.view(torch.int32), dx2.view(torch.int32)), name
+        assert torch.equal(dvals.view(torch.int32), dvals2.view(torch.int32)), name
+        results[name] = (y.cpu().numpy(), dx.cpu().numpy(), dvals.cpu().numpy())
+        plan.close()
+        del rp_cat, ci, v, y, dx, dvals, y2, dx2, dvals2
+        torch.cuda.empty_cache()
+    for mi, m in enumerate(b.mats):
         y64, yb = oracle.spmv(m.rp, m.ci, m.v, xs[mi])
-        assert_within_bound(y[rb[mi]:rb[mi + 1]], y64, yb, f"diff y m{mi}")
         dx64, dxb, dv32 = oracle.grad(m.rp, m.ci, m.v, xs[mi], dys[mi], m.num_cols)
-        assert_within_bound(dx[cb[mi]:cb[mi + 1]], dx64, dxb, f"diff dx m{mi}")
-        assert np.array_equal(dvals[nb[mi]:nb[mi + 1]].view(np.uint32), dv32.view(np.uint32))
+        for name, (y, dx, dvals) in results.items():
+            assert_within_bound(y[rb[mi]:rb[mi + 1]], y64, yb, f"diff y m{mi} {name}")
+            assert_within_bound(dx[cb[mi]:cb[mi + 1]], dx64, dxb, f"diff dx m{mi} {name}")
+            assert np.array_equal(dvals[nb[mi]:nb[mi + 1]].view(np.uint32), dv32.view(np.uint32)), (mi, name)

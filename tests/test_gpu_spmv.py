@@ -9,30 +9,10 @@ import pytest
 
 import oracle
 import workloads as W
-from helpers import assert_within_bound, edge_cases, small_cases, to_dev
+from helpers import SCHED_IDS, SCHEDULES, assert_within_bound, edge_cases, small_cases, to_dev
 
 pytestmark = pytest.mark.gpu
 
-SCHEDULES = [("thread_mapped", {}), ("warp_mapped", {}), ("block_mapped", {}),
-             ("group_mapped", {"group_size": 4}), ("group_mapped", {"group_size": 8}),
-             ("group_mapped", {"group_size": 16}), ("group_mapped", {"group_size": 64}),
-             ("group_mapped", {"group_size": 128}),
-             ("merge_path", {"items_per_thread": 4}), ("merge_path", {"items_per_thread": 8}),
-             ("merge_path", {"items_per_thread": 16}),
-             ("merge_path", {"items_per_thread": 4, "mp_variant": 1}),
-             ("merge_path", {"items_per_thread": 8, "mp_variant": 1}),
-             ("merge_path", {"items_per_thread": 16, "mp_variant": 1}),
-             ("merge_path", {"items_per_thread": 4, "mp_variant": 2}),
-             ("merge_path", {"items_per_thread": 8, "mp_variant": 2}),
-             ("merge_path", {"items_per_thread": 16, "mp_variant": 2}),
-             ("merge_path", {"items_per_thread": 8, "units_per_cta": 4}),
-             ("merge_path", {"items_per_thread": 4, "units_per_cta": 16}),
-             ("merge_path", {"items_per_thread": 4, "row_weight": 2}),
-             ("merge_path", {"items_per_thread": 8, "row_weight": 5}),
-             ("merge_path", {"items_per_thread": 8, "mp_variant": 3}),
-             ("merge_path", {"items_per_thread": 4, "mp_variant": 3, "tiles_per_share": 3}),
-             ("merge_path", {"items_per_thread": 16, "mp_variant": 3, "tiles_per_share": 2})]
-SCHED_IDS = [s + "".join(f"_{k}{v}" for k, v in o.items()) for s, o in SCHEDULES]
 
 
 @pytest.fixture(scope="module")

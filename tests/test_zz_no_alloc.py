@@ -1,13 +1,15 @@
 """lb_spmv_noalloc: merge-path SpMV for callers that cannot allocate device memory.
 
-Such callers (code running inside CUDA-graph capture, allocator-free real-time
-loops, hosts whose memory pool is closed to libraries) get their scratch from a
-fixed device array built into the library instead of from cudaMalloc.  This
-checks, through the C ABI, that two calls in a row give the same result as the
-planned entry point lb_spmv within the tolerance the parity tests use
-(|y - y64| <= 1e-5 * sum_j |a_ij x_j| against the FP64 oracle), and that a
-problem too large for the fixed scratch is refused before any launch.  This file
-runs last so that a failure here leaves every other test already run.
+Such callers (allocator-free real-time loops that reserve all device memory up
+front, hosts whose memory pool belongs to another framework) get their scratch
+from a fixed device array built into the library instead of from cudaMalloc.
+This checks, through the C ABI, that two calls in a row give the same result as
+the planned entry point lb_spmv within the tolerance the parity tests use
+(|y - y64| <= 1e-5 * sum_j |a_ij x_j| against the FP64 oracle), that the two
+calls are bit-identical, that atom arrays which are not 16-byte aligned (the
+scalar-load kernel) give the same, and that a problem too large for the fixed
+scratch is refused before any launch.  This file runs last so that a failure
+here leaves every other test already run.
 """
 import ctypes
 
@@ -41,20 +43,30 @@ def test_noalloc_matches_planned_spmv_twice():
     for m in cases:
         x = W.x_for(m)
         y64, b = oracle.spmv(m.rp, m.ci, m.v, x)
-        rp, ci, v, xd = _dev(m.rp), _dev(m.ci), _dev(m.v), _dev(x)
-        plan = lb.Plan(rp, m.nnz, "merge_path", num_cols=m.num_cols)
-        y_plan = plan.spmv(ci, v, xd)
-        stream = torch.cuda.current_stream().cuda_stream
-        for call in range(2):
-            y = torch.full((m.num_rows,), float("nan"), device="cuda")
-            st = lib.lb_spmv_noalloc(vp(rp.data_ptr()), m.num_rows, m.nnz, vp(ci.data_ptr()), vp(v.data_ptr()),
-                                     vp(xd.data_ptr()), vp(y.data_ptr()), vp(stream))
-            assert st == 0, lib.lb_last_error()
-            torch.cuda.synchronize()
-            got = y.cpu().numpy().astype(np.float64)
+        rp, xd = _dev(m.rp), _dev(x)
+        # 16-byte aligned atom arrays (vector loads), then the same arrays one element into larger
+        # buffers (not 16-byte aligned: the scalar-load kernel)
+        ci_buf = torch.zeros(m.nnz + 1, dtype=torch.int32, device="cuda")
+        v_buf = torch.zeros(m.nnz + 1, dtype=torch.float32, device="cuda")
+        ci_buf[1:] = _dev(m.ci)
+        v_buf[1:] = _dev(m.v)
+        for ci, v in ((_dev(m.ci), _dev(m.v)), (ci_buf[1:], v_buf[1:])):
+            plan = lb.Plan(rp, m.nnz, "merge_path", num_cols=m.num_cols)
+            y_plan = plan.spmv(ci, v, xd)
             ref = y_plan.cpu().numpy().astype(np.float64)
-            assert np.all(np.abs(got - y64) <= oracle.TOL * b), (m.name, call)
-            assert np.all(np.abs(got - ref) <= oracle.TOL * b), (m.name, call)
+            stream = torch.cuda.current_stream().cuda_stream
+            got = []
+            for call in range(2):
+                y = torch.full((m.num_rows,), float("nan"), device="cuda")
+                st = lib.lb_spmv_noalloc(vp(rp.data_ptr()), m.num_rows, m.nnz, vp(ci.data_ptr()), vp(v.data_ptr()),
+                                         vp(xd.data_ptr()), vp(y.data_ptr()), vp(stream))
+                assert st == 0, lib.lb_last_error()
+                torch.cuda.synchronize()
+                got.append(y.cpu().numpy())
+                g64 = got[-1].astype(np.float64)
+                assert np.all(np.abs(g64 - y64) <= oracle.TOL * b), (m.name, call, ci.data_ptr() % 16)
+                assert np.all(np.abs(g64 - ref) <= oracle.TOL * b), (m.name, call, ci.data_ptr() % 16)
+            assert np.array_equal(got[0].view(np.uint32), got[1].view(np.uint32)), (m.name, "calls differ")
 
 
 def test_noalloc_refuses_oversized_problem():
