@@ -323,8 +323,28 @@ typedef struct lb_tune_result_t {
 lb_status_t lb_autotune(const int32_t* tile_offsets, int32_t num_tiles, int32_t num_atoms, const int32_t* col_idx,
                         const float* vals, const float* x, float* y, const lb_tune_opts_t* opts,
                         lb_tune_result_t* result, lb_plan_t* out_plan, void* stream);
-/* Empties the autotuner's process-wide cache. */
+/* Empties the autotuner's process-wide cache (in memory; files are not touched). */
 void lb_autotune_cache_clear(void);
+/* Entries in the process-wide cache. */
+int32_t lb_autotune_cache_size(void);
+/*
+ * Persisted cache.  lb_autotune_cache_save writes every entry of the
+ * process-wide cache to `path` (host string), one JSON object per line: the
+ * key (GPU name / SM count / compute capability, rows, atoms, columns, the
+ * fingerprint, candidate families, cold-L2 flag) and the full result table;
+ * it writes `path`.tmp first and renames it over `path`.
+ * lb_autotune_cache_load merges the entries of such a file into the cache
+ * (an entry with the same key is replaced) and reports in *loaded (may be
+ * NULL) how many it took; lines that do not parse, or that another library
+ * version wrote, are skipped.  When the environment variable
+ * LB_AUTOTUNE_CACHE names a file, lb_autotune loads it once per process
+ * before its first lookup (a missing file is not an error) and saves the whole
+ * cache to it after every new tuning, so a later process finds the choice
+ * without timing.  Entries apply only to a GPU with the same identity.
+ * Errors: LB_ERR_INVALID_ARG (empty path, file not readable / writable).
+ */
+lb_status_t lb_autotune_cache_save(const char* path);
+lb_status_t lb_autotune_cache_load(const char* path, int32_t* loaded);
 /* ------------------------------------------------------------------ SpMM -- */
 /*
  * C = A B for a dense row-major B (Sec. 7, Listing 4: the SpMV loop with one

@@ -85,6 +85,9 @@ SIGNATURES = {
     "lb_autotune": (I32, [VP, I32, I32, VP, VP, VP, VP, ctypes.POINTER(TuneOpts), ctypes.POINTER(TuneResult), PLANP,
                           VP]),
     "lb_autotune_cache_clear": (None, []),
+    "lb_autotune_cache_size": (I32, []),
+    "lb_autotune_cache_save": (I32, [ctypes.c_char_p]),
+    "lb_autotune_cache_load": (I32, [ctypes.c_char_p, ctypes.POINTER(I32)]),
     "lb_coo_to_csr": (I32, [I32, I32, VP, VP, VP, VP, VP, VP, VP]),
     "lb_csc_to_csr": (I32, [I32, I32, I32, VP, VP, VP, VP, VP, VP, VP]),
     "lb_sssp": (I32, [VP, I32, I32, VP, VP, I32, I32, VP, ctypes.POINTER(I32), VP]),

@@ -4,6 +4,8 @@
 // rule is kept as the prior -- its pick is timed first and wins ties -- and
 // the measurement decides.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -48,9 +50,218 @@ struct Candidate {
   int row_weight = 1;  // merge-path variant 0: weight of a row end in the shares
 };
 
-using Key = std::tuple<int, int32_t, int32_t, int32_t, uint64_t, int32_t, int32_t>;
+// Cache key: the GPU (name / SM count / compute capability, so that a cache
+// file moves only between identical devices), sizes, fingerprint, candidate
+// families and the cold-L2 flag.
+using Key = std::tuple<std::string, int32_t, int32_t, int32_t, uint64_t, int32_t, int32_t>;
 std::mutex g_cache_mu;
 std::map<Key, lb_tune_result_t> g_cache;
+bool g_env_loaded = false;  // LB_AUTOTUNE_CACHE read into g_cache (once per process)
+
+std::string device_ident(int dev) {
+  cudaDeviceProp pr;
+  if (cudaGetDeviceProperties(&pr, dev) != cudaSuccess) return "unknown";
+  return std::string(pr.name) + "/" + std::to_string(pr.multiProcessorCount) + "/" + std::to_string(pr.major) + "." +
+         std::to_string(pr.minor);
+}
+
+// ---- persisted cache: one JSON object per line, written and read only here --
+//
+// {"format":"lb_autotune_cache","version":V,"device":"NAME/SMS/CC","rows":R,"atoms":N,"cols":C,
+//  "fingerprint":"0x...","families":F,"cold_l2":0|1,"best":b,"heuristic":h,"best_schedule":s,
+//  "best_opts":[12 ints of lb_plan_opts_t],"candidates":[[schedule,ipt,group,variant,units,row_weight,
+//  status,reps,ms,gbps],...]}
+constexpr int kOptsInts = (int)(sizeof(lb_plan_opts_t) / sizeof(int32_t));
+
+std::string entry_line(const Key& k, const lb_tune_result_t& r) {
+  std::string out;
+  char buf[512];
+  std::string dev = std::get<0>(k);
+  for (char& ch : dev)
+    if (ch == '"' || ch == '\\' || (unsigned char)ch < 0x20) ch = '_';
+  std::snprintf(buf, sizeof(buf),
+                "{\"format\":\"lb_autotune_cache\",\"version\":%d,\"device\":\"%s\",\"rows\":%d,\"atoms\":%d,"
+                "\"cols\":%d,\"fingerprint\":\"0x%016llx\",\"families\":%d,\"cold_l2\":%d,\"best\":%d,"
+                "\"heuristic\":%d,\"best_schedule\":%d,\"best_opts\":[",
+                (int)lb_version(), dev.c_str(), std::get<1>(k), std::get<2>(k), std::get<3>(k),
+                (unsigned long long)std::get<4>(k), std::get<5>(k), std::get<6>(k), r.best, r.heuristic,
+                r.best_schedule);
+  out += buf;
+  const int32_t* o = reinterpret_cast<const int32_t*>(&r.best_opts);
+  for (int i = 0; i < kOptsInts; ++i) {
+    std::snprintf(buf, sizeof(buf), "%s%d", i ? "," : "", o[i]);
+    out += buf;
+  }
+  out += "],\"candidates\":[";
+  for (int i = 0; i < r.num_candidates; ++i) {
+    const lb_tune_candidate_t& c = r.candidates[i];
+    std::snprintf(buf, sizeof(buf), "%s[%d,%d,%d,%d,%d,%d,%d,%d,%.9g,%.9g]", i ? "," : "", c.schedule,
+                  c.items_per_thread, c.group_size, c.mp_variant, c.units_per_cta, c.row_weight, c.status, c.reps,
+                  (double)c.ms, (double)c.gbps);
+    out += buf;
+  }
+  out += "]}\n";
+  return out;
+}
+
+// value after "key": in one line (nullptr if absent)
+const char* field(const std::string& line, const char* key) {
+  const std::string pat = std::string("\"") + key + "\":";
+  const size_t at = line.find(pat);
+  return at == std::string::npos ? nullptr : line.c_str() + at + pat.size();
+}
+
+bool field_ll(const std::string& line, const char* key, long long& v) {
+  const char* p = field(line, key);
+  if (!p) return false;
+  char* end = nullptr;
+  v = std::strtoll(p, &end, 10);
+  return end != p;
+}
+
+bool field_str(const std::string& line, const char* key, std::string& v) {
+  const char* p = field(line, key);
+  if (!p || *p != '"') return false;
+  const char* e = std::strchr(p + 1, '"');
+  if (!e) return false;
+  v.assign(p + 1, e);
+  return true;
+}
+
+// every number inside the (possibly nested) array that follows "key":
+bool field_nums(const std::string& line, const char* key, std::vector<double>& v) {
+  const char* p = field(line, key);
+  if (!p || *p != '[') return false;
+  int depth = 0;
+  v.clear();
+  while (*p) {
+    if (*p == '[') {
+      ++depth;
+      ++p;
+    } else if (*p == ']') {
+      if (--depth == 0) return true;
+      ++p;
+    } else if (*p == ',' || *p == ' ') {
+      ++p;
+    } else {
+      char* end = nullptr;
+      const double d = std::strtod(p, &end);
+      if (end == p) return false;
+      v.push_back(d);
+      p = end;
+    }
+  }
+  return false;
+}
+
+// one line -> (key, result); false if it is not a valid entry of this library version
+bool parse_entry(const std::string& line, Key& k, lb_tune_result_t& r) {
+  long long ver, rows, atoms, cols, fam, cold, best, heur, bs;
+  std::string dev, fps, fmt;
+  std::vector<double> opts, cands;
+  if (!field_str(line, "format", fmt) || fmt != "lb_autotune_cache" || !field_ll(line, "version", ver) ||
+      ver != lb_version() || !field_str(line, "device", dev) || !field_ll(line, "rows", rows) ||
+      !field_ll(line, "atoms", atoms) || !field_ll(line, "cols", cols) || !field_str(line, "fingerprint", fps) ||
+      !field_ll(line, "families", fam) || !field_ll(line, "cold_l2", cold) || !field_ll(line, "best", best) ||
+      !field_ll(line, "heuristic", heur) || !field_ll(line, "best_schedule", bs) ||
+      !field_nums(line, "best_opts", opts) || !field_nums(line, "candidates", cands))
+    return false;
+  if ((int)opts.size() != kOptsInts || cands.size() % 10 != 0 || cands.size() / 10 > LB_TUNE_MAX_CANDIDATES ||
+      cands.empty() || best < 0 || best >= (long long)(cands.size() / 10) || heur >= (long long)(cands.size() / 10))
+    return false;
+  std::memset(&r, 0, sizeof(r));
+  r.num_candidates = (int32_t)(cands.size() / 10);
+  r.best = (int32_t)best;
+  r.heuristic = (int32_t)heur;
+  r.best_schedule = (int32_t)bs;
+  int32_t* o = reinterpret_cast<int32_t*>(&r.best_opts);
+  for (int i = 0; i < kOptsInts; ++i) o[i] = (int32_t)opts[i];
+  for (int i = 0; i < r.num_candidates; ++i) {
+    const double* c = cands.data() + 10 * i;
+    lb_tune_candidate_t& t = r.candidates[i];
+    t.schedule = (int32_t)c[0];
+    t.items_per_thread = (int32_t)c[1];
+    t.group_size = (int32_t)c[2];
+    t.mp_variant = (int32_t)c[3];
+    t.units_per_cta = (int32_t)c[4];
+    t.row_weight = (int32_t)c[5];
+    t.status = (int32_t)c[6];
+    t.reps = (int32_t)c[7];
+    t.ms = (float)c[8];
+    t.gbps = (float)c[9];
+  }
+  const uint64_t fp = std::strtoull(fps.c_str(), nullptr, 16);
+  k = Key{dev, (int32_t)rows, (int32_t)atoms, (int32_t)cols, fp, (int32_t)fam, (int32_t)cold};
+  return true;
+}
+
+// caller holds g_cache_mu
+lb_status_t load_locked(const char* path, int32_t* loaded) {
+  if (loaded) *loaded = 0;
+  FILE* f = std::fopen(path, "r");
+  if (!f) {
+    set_error(std::string("autotune cache: cannot open ") + path);
+    return LB_ERR_INVALID_ARG;
+  }
+  std::string line;
+  char buf[4096];
+  int32_t n = 0;
+  while (std::fgets(buf, sizeof(buf), f)) {
+    line += buf;
+    if (line.empty() || line.back() != '\n') {
+      if (!std::feof(f)) continue;  // a line longer than the buffer: keep reading
+    }
+    Key k;
+    lb_tune_result_t r;
+    if (parse_entry(line, k, r)) {
+      g_cache[k] = r;
+      ++n;
+    }
+    line.clear();
+  }
+  std::fclose(f);
+  if (loaded) *loaded = n;
+  return LB_OK;
+}
+
+// caller holds g_cache_mu; written to a temporary file first, then renamed over `path`
+lb_status_t save_locked(const char* path) {
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "w");
+  if (!f) {
+    set_error(std::string("autotune cache: cannot write ") + tmp);
+    return LB_ERR_INVALID_ARG;
+  }
+  bool ok = true;
+  for (const auto& kv : g_cache) {
+    const std::string l = entry_line(kv.first, kv.second);
+    ok = ok && std::fwrite(l.data(), 1, l.size(), f) == l.size();
+  }
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok || std::rename(tmp.c_str(), path) != 0) {
+    std::remove(tmp.c_str());
+    set_error(std::string("autotune cache: cannot write ") + path);
+    return LB_ERR_INVALID_ARG;
+  }
+  return LB_OK;
+}
+
+// the file named by LB_AUTOTUNE_CACHE, if any (caller holds g_cache_mu)
+const char* env_cache_path() {
+  const char* p = std::getenv("LB_AUTOTUNE_CACHE");
+  return p && *p ? p : nullptr;
+}
+
+void env_load_locked() {
+  if (g_env_loaded) return;
+  g_env_loaded = true;
+  const char* p = env_cache_path();
+  if (!p) return;
+  FILE* f = std::fopen(p, "r");
+  if (!f) return;  // no file yet: the first tuning creates it
+  std::fclose(f);
+  load_locked(p, nullptr);
+}
 
 std::vector<Candidate> candidate_list(lb_schedule_t prior, int families, bool aligned) {
   std::vector<Candidate> v;
@@ -158,6 +369,29 @@ void lb_autotune_cache_clear(void) {
   g_cache.clear();
 }
 
+int32_t lb_autotune_cache_size(void) {
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  return (int32_t)g_cache.size();
+}
+
+lb_status_t lb_autotune_cache_save(const char* path) {
+  if (!path || !*path) {
+    set_error("lb_autotune_cache_save: path must not be empty");
+    return LB_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  return save_locked(path);
+}
+
+lb_status_t lb_autotune_cache_load(const char* path, int32_t* loaded) {
+  if (!path || !*path) {
+    set_error("lb_autotune_cache_load: path must not be empty");
+    return LB_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  return load_locked(path, loaded);
+}
+
 lb_status_t lb_autotune(const int32_t* tile_offsets, int32_t num_tiles, int32_t num_atoms, const int32_t* col_idx,
                         const float* vals, const float* x, float* y, const lb_tune_opts_t* opts,
                         lb_tune_result_t* result, lb_plan_t* out_plan, void* stream) {
@@ -211,10 +445,12 @@ lb_status_t lb_autotune(const int32_t* tile_offsets, int32_t num_tiles, int32_t 
     LB_CUDA_TRY(e);
     fp = h;
   }
-  const Key key{dev, num_tiles, num_atoms, C, fp, families, opts->cold_l2 ? 1 : 0};
+  const Key key{use_cache ? device_ident(dev) : std::string(), num_tiles, num_atoms, C, fp, families,
+                opts->cold_l2 ? 1 : 0};
   bool hit = false;
   if (use_cache) {
     std::lock_guard<std::mutex> lock(g_cache_mu);
+    env_load_locked();
     auto it = g_cache.find(key);
     if (it != g_cache.end()) {
       *result = it->second;
@@ -276,6 +512,8 @@ lb_status_t lb_autotune(const int32_t* tile_offsets, int32_t num_tiles, int32_t 
     if (use_cache) {
       std::lock_guard<std::mutex> lock(g_cache_mu);
       g_cache[key] = *result;
+      // persist the new entry when LB_AUTOTUNE_CACHE names a file (a failed write is not an error of the tuning)
+      if (const char* path = env_cache_path()) save_locked(path);
     }
   }
 

@@ -1402,12 +1402,24 @@ __global__ void __launch_bounds__(256) mp_expand_warp_kernel(MpArgs a) {
           m1 = __ldg(sm + k + 1);
           xb0 = __ldg(a.vec_base + m0);
         }
+        // whether the launch validates column indices is tested once per tile (the same
+        // answer for every warp), so an unvalidated launch gathers without a test per atom
+        if (a.atoms.check <= 0) {
 #pragma unroll
-        for (int q = 0; q < IPT; ++q) {
-          const int l = s0 + q - off;
-          xv[q] = (unsigned)l < (unsigned)nnz
-                      ? a.atoms.gather(c_cur[q], atom_xbase<XB>(a, m0, m1, xb0, (int64_t)j0 + l))
-                      : 0.f;
+          for (int q = 0; q < IPT; ++q) {
+            const int l = s0 + q - off;
+            xv[q] = (unsigned)l < (unsigned)nnz
+                        ? __ldg(a.atoms.vec + atom_xbase<XB>(a, m0, m1, xb0, (int64_t)j0 + l) + c_cur[q])
+                        : 0.f;
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < IPT; ++q) {
+            const int l = s0 + q - off;
+            xv[q] = (unsigned)l < (unsigned)nnz
+                        ? a.atoms.gather(c_cur[q], atom_xbase<XB>(a, m0, m1, xb0, (int64_t)j0 + l))
+                        : 0.f;
+          }
         }
       }
       // next tile's columns and row ends, in flight while this one is expanded

@@ -328,7 +328,24 @@ def sssp(tile_offsets: torch.Tensor, col_idx: torch.Tensor, weights: torch.Tenso
 
 
 def autotune_cache_clear():
+    """Empties the autotuner's in-memory cache (files are not touched)."""
     _lib.load().lb_autotune_cache_clear()
+
+
+def autotune_cache_size() -> int:
+    return int(_lib.load().lb_autotune_cache_size())
+
+
+def autotune_cache_save(path: str):
+    """Writes the autotuner's cache to ``path`` (one JSON object per line)."""
+    check(_lib.load().lb_autotune_cache_save(str(path).encode()), "lb_autotune_cache_save")
+
+
+def autotune_cache_load(path: str) -> int:
+    """Merges the entries of a file written by autotune_cache_save; returns how many were taken."""
+    n = ctypes.c_int32(0)
+    check(_lib.load().lb_autotune_cache_load(str(path).encode(), ctypes.byref(n)), "lb_autotune_cache_load")
+    return int(n.value)
 
 
 class BatchPlan:

@@ -133,3 +133,33 @@ def test_selftest_rejects_unknown_case_without_launching(lib):
     assert lib.lb_selftest(0, None) == 1
     assert lib.lb_selftest(3, None) == 1
     assert b"which" in lib.lb_last_error()
+
+
+def test_autotune_cache_file_round_trip(lib, tmp_path):
+    """The persisted autotuner cache (no GPU needed): a file of entries loads,
+    saves back to the same text, reloads after a clear; lines of another
+    library version or that do not parse are skipped."""
+    ver = lib.lb_version()
+    cands = "[[3,8,0,0,1,1,0,5,0.5,1900.25],[3,4,0,0,1,2,0,5,0.25,3800.5],[0,0,0,0,1,1,0,1,12.5,7.75]]"
+    opts = ",".join(str(v) for v in (1000000, 4, 0, 0, 0, 0, 0, 1, 0, 0, 2, 0))
+
+    def line(v, rows, fp):
+        return ('{"format":"lb_autotune_cache","version":%d,"device":"NVIDIA GB300/152/10.3","rows":%d,'
+                '"atoms":20000016,"cols":1000000,"fingerprint":"0x%016x","families":15,"cold_l2":1,"best":1,'
+                '"heuristic":0,"best_schedule":3,"best_opts":[%s],"candidates":%s}\n' % (v, rows, fp, opts, cands))
+    good = [line(ver, 1000000, 0x0123456789abcdef), line(ver, 5, 0xfedcba9876543210)]
+    src = tmp_path / "cache.jsonl"
+    src.write_text(good[0] + line(ver + 1, 7, 1) + "not json\n" + good[1])
+    lib.lb_autotune_cache_clear()
+    n = ctypes.c_int32(-1)
+    assert lib.lb_autotune_cache_load(str(src).encode(), ctypes.byref(n)) == 0
+    assert n.value == 2 and lib.lb_autotune_cache_size() == 2
+    out = tmp_path / "saved.jsonl"
+    assert lib.lb_autotune_cache_save(str(out).encode()) == 0
+    assert sorted(out.read_text().splitlines(keepends=True)) == sorted(good)
+    lib.lb_autotune_cache_clear()
+    assert lib.lb_autotune_cache_size() == 0
+    assert lib.lb_autotune_cache_load(str(out).encode(), ctypes.byref(n)) == 0 and n.value == 2
+    lib.lb_autotune_cache_clear()
+    assert lib.lb_autotune_cache_load(str(tmp_path / "missing.jsonl").encode(), None) == 1
+    assert lib.lb_autotune_cache_save(b"") == 1

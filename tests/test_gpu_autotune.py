@@ -104,3 +104,39 @@ def test_autotune_family_mask_and_edge_cases(lbmod):
     # num_cols missing with atoms present: refused before any launch
     with pytest.raises(_lib.LBError):
         lbmod.autotune(rp, ci, v, xd, num_cols=0, use_cache=False)
+
+
+_CHILD = r"""
+import json, sys
+sys.path.insert(0, {root!r})
+import torch, workloads as W, paper_2301_04792_gb300 as lb
+m = W.powerlaw(30_000, 30_000, 500_000, lmax=20_000, plant_long=False, seed=24)
+rp, ci, v, x = (torch.from_numpy(a).cuda() for a in (m.rp, m.ci, m.v, W.x_for(m)))
+_, rep = lb.autotune(rp, ci, v, x, num_cols=m.num_cols, reps=2)
+print(json.dumps({{"from_cache": rep["from_cache"], "best": rep["best"], "ms": [c["ms"] for c in rep["candidates"]],
+                  "size": lb.autotune_cache_size()}}))
+"""
+
+
+def test_autotune_cache_file_skips_timing_in_a_second_process(lbmod, tmp_path):
+    """With LB_AUTOTUNE_CACHE set, the first process times every candidate and
+    writes the file; a second process finds the entry and times nothing, with
+    the same winner and the same table."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    path = tmp_path / "tune.jsonl"
+    env = dict(os.environ, LB_AUTOTUNE_CACHE=str(path))
+    runs = []
+    for _ in range(2):
+        out = subprocess.run([sys.executable, "-c", _CHILD.format(root=root)], env=env, capture_output=True, text=True,
+                             timeout=600)
+        assert out.returncode == 0, out.stderr[-2000:]
+        runs.append(json.loads(out.stdout.strip().splitlines()[-1]))
+    assert path.exists() and len(path.read_text().splitlines()) == 1
+    assert not runs[0]["from_cache"] and runs[1]["from_cache"]
+    assert runs[0]["best"] == runs[1]["best"]
+    assert runs[0]["ms"] == runs[1]["ms"]
+    assert runs[1]["size"] == 1
