@@ -670,6 +670,20 @@ def run_ours(args, ws, rank, local):
     for i in range(3):
         probe(i)
     probe_ms = statistics.median(time_launches(torch, probe, 20 if args.ncu else 50, stream))
+    # the other gather path: TMA row gathers (tile::gather4) of x into shared memory
+    n_tma = N - (N % 128)
+    tgrid = lib.lb_probe_gather_tma_grid()
+    tma_out = torch.empty(max(1, tgrid) * 256, device=device)
+    tma_err = torch.zeros(1, dtype=torch.int32, device=device)
+
+    def probe_tma(i):
+        _lib.check(lib.lb_probe_gather_tma(vp(ci_d[i % copies].data_ptr()), vp(v_d[i % copies].data_ptr()),
+                                           vp(x_d.data_ptr()), n_tma, C, vp(tma_out.data_ptr()), tgrid,
+                                           vp(tma_err.data_ptr()), vp(sp)), "lb_probe_gather_tma")
+    for i in range(3):
+        probe_tma(i)
+    probe_tma_ms = statistics.median(time_launches(torch, probe_tma, 20 if args.ncu else 50, stream))
+    tma_probe_ok = int(tma_err.item()) == 0
 
     peak, peak_kind = measured_peaks()
     kern_ms = statistics.median(durs)
@@ -681,7 +695,11 @@ def run_ours(args, ws, rank, local):
                 "gather_ceiling": {"probe": "lb_probe_gather: stream the same col_idx/vals, gather x, nothing else",
                                    "probe_ms": round(probe_ms, 5),
                                    "spmv_GBps_at_ceiling": round(byts / (probe_ms * 1e-3) / 1e9, 2),
-                                   "frac": round(probe_ms / kern_ms, 4)}}
+                                   "frac": round(probe_ms / kern_ms, 4),
+                                   "tma_gather4_probe_ms": round(probe_tma_ms, 5),
+                                   "tma_gather4_probe_ok": tma_probe_ok,
+                                   "tma_note": "lb_probe_gather_tma: the same stream with x gathered by TMA "
+                                               "tile::gather4 row copies into shared memory"}}
 
     print(f"[bench] merge-path {value:.1f} GB/s ({step_ms * 1e3:.2f} us/step), kernel {achieved:.1f} GB/s, "
           f"parity {parity_ok}", file=sys.stderr, flush=True)
@@ -934,10 +952,18 @@ def run_case(name: str):
         grid = lib.lb_probe_gather_grid()
         out = torch.empty(grid * 256, device=dev)
         vp = ctypes.c_void_p
+        tgrid = lib.lb_probe_gather_tma_grid()
+        tout = torch.empty(max(grid, tgrid) * 256, device=dev)
+        err = torch.zeros(1, dtype=torch.int32, device=dev)
+        sp = vp(torch.cuda.current_stream().cuda_stream)
         for _ in range(3):
             _lib.check(lib.lb_probe_gather(vp(ci.data_ptr()), vp(v.data_ptr()), vp(x.data_ptr()), m.nnz - m.nnz % 4,
-                                           vp(out.data_ptr()), grid, vp(torch.cuda.current_stream().cuda_stream)),
-                       "lb_probe_gather")
+                                           vp(out.data_ptr()), grid, sp), "lb_probe_gather")
+            _lib.check(lib.lb_probe_gather_tma(vp(ci.data_ptr()), vp(v.data_ptr()), vp(x.data_ptr()),
+                                               m.nnz - m.nnz % 128, m.num_cols, vp(tout.data_ptr()), tgrid,
+                                               vp(err.data_ptr()), sp), "lb_probe_gather_tma")
+        torch.cuda.synchronize()
+        assert int(err.item()) == 0, "TMA probe wait gave up"
     elif name == "sssp_rmat":
         g = W.rmat()
         rp, ci, w = d(g.rp, g.ci, g.v.astype(np.float32))

@@ -476,6 +476,25 @@ lb_status_t lb_probe_gather(const int32_t* idx, const float* vals, const float* 
                             int32_t grid, void* stream);
 int32_t lb_probe_gather_grid(void);
 /*
+ * The same measurement through the tensor-memory-accelerator gather path (no
+ * counterpart in the paper): x[num_x] is described to the TMA unit as rows of
+ * 8 floats, and each warp copies the rows holding its atoms' x entries into
+ * shared memory with cp.async.bulk.tensor ... tile::gather4 (four rows per
+ * copy, one copy per lane and 128 atoms per warp step, a two-slot ring per
+ * warp completed on mbarriers), then reduces sum vals[k] * x[idx[k]] to one
+ * float per thread into out[grid * 256].  idx, vals, x: device, 16-byte
+ * aligned; n a multiple of 128; an index at or past 8 * floor(num_x / 8)
+ * counts as x = 0 (no copy leaves the described rows).  grid = 0 picks the
+ * occupancy (lb_probe_gather_tma_grid).  Waits are bounded: a wait that gives
+ * up ORs 2 (the timeout bit) into *err (device int, caller-owned, cleared by
+ * the caller) and the kernel returns.  Async, no allocation.  Errors:
+ * LB_ERR_INVALID_ARG (sizes, NULL or unaligned buffers), LB_ERR_UNSUPPORTED
+ * (no tensor-map encoder in the driver), LB_ERR_CUDA.
+ */
+lb_status_t lb_probe_gather_tma(const int32_t* idx, const float* vals, const float* x, int64_t n, int32_t num_x,
+                                float* out, int32_t grid, int32_t* err, void* stream);
+int32_t lb_probe_gather_tma_grid(void);
+/*
  * Failure-detection self-test (no counterpart in the paper).  which = 1 runs
  * the merge-path look-back wait against a predecessor record that is never
  * published; which = 2 runs the bounded mbarrier wait of the bulk-copy kernel

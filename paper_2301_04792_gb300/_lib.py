@@ -101,6 +101,8 @@ SIGNATURES = {
     "lb_merge_diagonals": (I32, [I64, I32, I32, VP, SZ, ctypes.POINTER(SZ), ctypes.POINTER(I32)]),
     "lb_probe_gather": (I32, [VP, VP, VP, I64, VP, I32, VP]),
     "lb_probe_gather_grid": (I32, []),
+    "lb_probe_gather_tma": (I32, [VP, VP, VP, I64, I32, VP, I32, VP, VP]),
+    "lb_probe_gather_tma_grid": (I32, []),
     "lb_selftest": (I32, [I32, VP]),
     "lb_status_string": (ctypes.c_char_p, [I32]),
     "lb_last_error": (ctypes.c_char_p, []),

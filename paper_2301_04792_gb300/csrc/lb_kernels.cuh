@@ -27,6 +27,11 @@ constexpr int kStages = 3;         // shared-memory ring depth of the merge-path
 constexpr long long kSpinLimit = 1LL << 26;
 constexpr long long kLookbackSpins = 1LL << 22;  // with 64 ns sleeps: a few tenths of a second
 
+// resident CTAs per SM the look-back kernel is compiled for at items_per_thread 4
+#ifndef LB_LOOKBACK_IPT4_CTAS
+#define LB_LOOKBACK_IPT4_CTAS 4
+#endif
+
 // ------------------------------------------------------------- load helpers --
 
 __device__ __forceinline__ int ld_stream(const int* p) { return __ldcs(p); }
@@ -1209,7 +1214,7 @@ __device__ __forceinline__ bool look_back(const unsigned long long* records, int
 // Records carry the launch's epoch (ticket[2]), which the last CTA to finish
 // advances, so they need no reset between launches.
 template <int IPT, bool XB, bool PERM, bool VEC>
-__global__ void __launch_bounds__(256, IPT <= 8 ? 4 : 2) mp_spmv_lookback_kernel(MpArgs a) {
+__global__ void __launch_bounds__(256, IPT <= 4 ? LB_LOOKBACK_IPT4_CTAS : IPT <= 8 ? 4 : 2) mp_spmv_lookback_kernel(MpArgs a) {
   constexpr int WPB = 8;
   constexpr int kNarrow = 4;  // predecessors one lane walks before the warp-wide window takes over
   __shared__ WarpScratch<IPT> sc_all[WPB];
@@ -1227,6 +1232,42 @@ __global__ void __launch_bounds__(256, IPT <= 8 ? 4 : 2) mp_spmv_lookback_kernel
     float total;
     if (!look_back(a.records, p, epoch, total) && lane == 0 && a.status) atomicOr(a.status, kDevErrTimeout);
     if (lane == 0) add_to_first_row(p, total);
+  };
+  // The pending shares of this warp (all of whose predecessors' records are
+  // published or being published): each lane walks back from one of them
+  // through the records, nearest first, adding the partial sums up to the
+  // nearest FINAL one (or share 0); a run longer than kNarrow records goes to
+  // the warp-wide window instead.  Which of the two a share takes depends only
+  // on the data, and every share goes through this same code whether its list
+  // is resolved because it is full or because the warp has no shares left, so
+  // the order of every sum is fixed by the plan.
+  auto resolve_pending = [&](int npend) {
+    bool wide = false;
+    if (lane < npend) {
+      const int p = s_pend[warp][lane];
+      float total = 0.f;
+      bool done = false, gave_up = false;
+      for (int q = p - 1, n = 0; q >= 0 && n < kNarrow && !done && !gave_up; --q, ++n) {
+        unsigned long long w = 0;
+        for (long long spin = 0;; ++spin) {
+          w = *reinterpret_cast<volatile const unsigned long long*>(a.records + q);
+          if ((unsigned)(w >> 33) == epoch) break;
+          if (spin > kLookbackSpins) {
+            gave_up = true;
+            break;
+          }
+          __nanosleep(64);
+        }
+        if (gave_up) break;
+        total += __uint_as_float((unsigned)w);
+        done = ((w >> 32) & 1ull) || q == 0;
+      }
+      if (gave_up && a.status) atomicOr(a.status, kDevErrTimeout);
+      if (done || gave_up) add_to_first_row(p, total);
+      else wide = true;
+    }
+    for (unsigned m = __ballot_sync(kFull, wide); m; m &= m - 1) resolve(s_pend[warp][__ffs(m) - 1]);
+    __syncwarp();
   };
   int npend = 0;
 
@@ -1296,10 +1337,10 @@ __global__ void __launch_bounds__(256, IPT <= 8 ? 4 : 2) mp_spmv_lookback_kernel
     const bool has_end = c1.x > __ldg(&a.share_head[s].x);
     if (lane == 0 && s + 1 < a.num_workers) publish_record(a.records + s, epoch, has_end, carry);
     // resolved once the warp has no shares left (the records are published by then), one lane per
-    // pending share; a full list is resolved at once
+    // pending share; a full list is resolved at once, by the same code
     if (has_end && s > 0) {
       if (npend == 32) {
-        for (int q = 0; q < 32; ++q) resolve(s_pend[warp][q]);
+        resolve_pending(32);
         npend = 0;
       }
       if (lane == 0) s_pend[warp][npend] = s;
@@ -1319,34 +1360,7 @@ __global__ void __launch_bounds__(256, IPT <= 8 ? 4 : 2) mp_spmv_lookback_kernel
     carry = 0.f;
     taken = false;
   }
-  // Each lane walks back from one pending share through the records, nearest first, adding the
-  // partial sums up to the nearest FINAL one (or share 0); a run longer than kNarrow records goes to
-  // the warp-wide window instead.  Either way the order of the sums depends only on the data.
-  bool wide = false;
-  if (lane < npend) {
-    const int p = s_pend[warp][lane];
-    float total = 0.f;
-    bool done = false, gave_up = false;
-    for (int q = p - 1, n = 0; q >= 0 && n < kNarrow && !done && !gave_up; --q, ++n) {
-      unsigned long long w = 0;
-      for (long long spin = 0;; ++spin) {
-        w = *reinterpret_cast<volatile const unsigned long long*>(a.records + q);
-        if ((unsigned)(w >> 33) == epoch) break;
-        if (spin > kLookbackSpins) {
-          gave_up = true;
-          break;
-        }
-        __nanosleep(64);
-      }
-      if (gave_up) break;
-      total += __uint_as_float((unsigned)w);
-      done = ((w >> 32) & 1ull) || q == 0;
-    }
-    if (gave_up && a.status) atomicOr(a.status, kDevErrTimeout);
-    if (done || gave_up) add_to_first_row(p, total);
-    else wide = true;
-  }
-  for (unsigned m = __ballot_sync(kFull, wide); m; m &= m - 1) resolve(s_pend[warp][__ffs(m) - 1]);
+  resolve_pending(npend);
   // the last CTA to finish resets the share counter and advances the epoch
   if (cta_ticket(a, &s_last) && threadIdx.x == 0) {
     const unsigned e1 = (epoch + 1u) & 0x7fffffffu;
