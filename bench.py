@@ -336,7 +336,9 @@ def bench_configs(torch, lb, W, device, peak, cores):
     xs = [W.x_for(m, seed=i) for i, m in enumerate(b.mats)]
     x = torch.from_numpy(np.concatenate(xs)).to(device)
     y = torch.empty(int(rows.sum()), device=device)
-    bp = lb.BatchPlan(rows, cols, nnz, rp_cat, mp_variant=3, items_per_thread=4)
+    # the batch's schedule and tile size from the batch autotuner (cold L2, forward pass)
+    bp, brep = lb.batch_autotune(rows, cols, nnz, rp_cat, ci, v, x, passes="fwd", y_cat=y, reps=5, cold_l2=True,
+                                 use_cache=False)
     rb = np.concatenate([[0], np.cumsum(rows)])
     cb = np.concatenate([[0], np.cumsum(cols)])
     nb = np.concatenate([[0], np.cumsum(nnz)])
@@ -346,11 +348,25 @@ def bench_configs(torch, lb, W, device, peak, cores):
     from paper_2301_04792_gb300 import _lib
     lib = _lib.load()
     vp = ctypes.c_void_p
-    calls = [(p.handle, vp(ci.data_ptr() + 4 * int(nb[i])), vp(v.data_ptr() + 4 * int(nb[i])),
-              vp(x.data_ptr() + 4 * int(cb[i])), vp(y.data_ptr() + 4 * int(rb[i]))) for i, p in enumerate(plans)]
 
-    def per_matrix(sp):
-        for h, c_, v_, x_, y_ in calls:
+    def calls_for(ps):
+        return [(p.handle, vp(ci.data_ptr() + 4 * int(nb[i])), vp(v.data_ptr() + 4 * int(nb[i])),
+                 vp(x.data_ptr() + 4 * int(cb[i])), vp(y.data_ptr() + 4 * int(rb[i]))) for i, p in enumerate(ps)]
+    calls = calls_for(plans)
+    # every matrix's own schedule and tile size from the single-matrix autotuner (merge-path warp
+    # workers, thread-mapped and group-mapped candidates), launched matrix by matrix
+    tuned, tuned_names = [], {}
+    for i in range(b.num):
+        sl = slice(int(nb[i]), int(nb[i + 1]))
+        pt, rep_i = lb.autotune(rp_cat[rb[i] + i: rb[i + 1] + i + 1], ci[sl], v[sl], x[int(cb[i]):int(cb[i + 1])],
+                                num_cols=int(cols[i]), y=y[int(rb[i]):int(rb[i + 1])], reps=3, use_cache=False,
+                                families=_lib.TUNE_MP_WARP | _lib.TUNE_THREAD | _lib.TUNE_GROUP)
+        tuned.append(pt)
+        tuned_names[rep_i["best"]] = tuned_names.get(rep_i["best"], 0) + 1
+    tuned_calls = calls_for(tuned)
+
+    def per_matrix(sp, cl=None):
+        for h, c_, v_, x_, y_ in (calls if cl is None else cl):
             _lib.check(lib.lb_spmv(h, c_, v_, x_, y_, vp(sp)), "lb_spmv")
     s = torch.cuda.Stream(device=device)
     s.wait_stream(torch.cuda.current_stream())
@@ -365,6 +381,9 @@ def bench_configs(torch, lb, W, device, peak, cores):
     cap = torch.cuda.Stream(device=device)
     with torch.cuda.graph(gp, stream=cap):
         per_matrix(cap.cuda_stream)
+    gt = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gt, stream=cap):
+        per_matrix(cap.cuda_stream, tuned_calls)
     torch.cuda.synchronize()
 
     def timed(fn, reps=7):
@@ -388,6 +407,9 @@ def bench_configs(torch, lb, W, device, peak, cores):
     y_p = y.cpu().numpy()
     ok_p = all_within(oracle, [(m, xs[i], y_p[rb[i]:rb[i + 1]]) for i, m in enumerate(b.mats)], cores)
     t_pg = timed(gp.replay)
+    t_tg = timed(gt.replay)
+    y_t = y.cpu().numpy()
+    ok_t = all_within(oracle, [(m, xs[i], y_t[rb[i]:rb[i + 1]]) for i, m in enumerate(b.mats)], cores)
     R, C, N = int(rows.sum()), int(cols.sum()), int(nnz.sum())
     byts = 8 * N + 4 * (R + b.num) + 4 * C + 4 * R
     gbps = byts / (t_b * 1e-3) / 1e9
@@ -396,12 +418,16 @@ def bench_configs(torch, lb, W, device, peak, cores):
                        "speedup_vs_graph": round(t_pg / t_b, 3), "GBps": round(gbps, 2),
                        "frac_of_8TBps": round(gbps / 8000.0, 4), "frac_of_measured": round(gbps / peak, 4),
                        "GFLOPs": round(2 * N / (t_b * 1e-3) / 1e9, 2),
-                       "batch_plan": "merge_path_ipt4_v3", "per_matrix_plan": "merge_path_ipt8_v0 (library default)",
-                       "parity_all_rows": {"batched": ok_b, "per_matrix": ok_p}}
-    for p in plans:
+                       "batch_plan": brep["best"], "per_matrix_plan": "merge_path_ipt8_v0 (library default)",
+                       "batch_autotune_ms": {c["name"]: round(c["ms"], 4) for c in brep["candidates"]},
+                       "per_matrix_autotuned_graph_ms": round(t_tg, 4),
+                       "speedup_vs_per_matrix_autotuned": round(t_tg / t_b, 3),
+                       "per_matrix_autotuned_choices": tuned_names,
+                       "parity_all_rows": {"batched": ok_b, "per_matrix": ok_p, "per_matrix_autotuned": ok_t}}
+    for p in plans + tuned:
         p.close()
     bp.close()
-    del g, gp
+    del g, gp, gt
     torch.cuda.synchronize()
     return out
 
@@ -464,8 +490,9 @@ def bench_batched(torch, lb, W, device, cores=1, reps=5):
                   "merge_path_ipt4_v3": dict(items_per_thread=4, mp_variant=3)}
     plains = {k: make_plain(**kw) for k, kw in plain_cfgs.items()}
 
-    # the batch: look-back shares (variant 3), items_per_thread 4 for both tile sets
-    bp = lb.BatchPlan(rows, cols, nnz, rp_cat, mp_variant=3, items_per_thread=4)
+    # the batch's schedule and tile size from the batch autotuner, timed over fwd + dx + dvals
+    bp, brep = lb.batch_autotune(rows, cols, nnz, rp_cat, ci, v, x, dy, passes="fwd+dx+dvals", y_cat=y, dx_cat=dx,
+                                 dvals_cat=dv, reps=3, use_cache=False)
     bp.prepare_backward(ci)
 
     def batched_step():
@@ -542,7 +569,8 @@ def bench_batched(torch, lb, W, device, cores=1, reps=5):
     bwd_dv = 8 * N + 4 * (R + b.num) + 4 * R + 4 * C
     byts = fwd + bwd_dx + bwd_dv
     out = {"workload": f"{b.num} power-law matrices 2^20 x 2^20, ~16M nnz each (total {N} nnz)",
-           "batch_plan": "merge_path_ipt4_v3 (look-back shares), one launch per pass, CUDA graph",
+           "batch_plan": brep["best"] + " (batch autotuner over fwd + dx + dvals), one launch per pass, CUDA graph",
+           "batch_autotune_ms": {c["name"]: round(c["ms"], 4) for c in brep["candidates"]},
            "plain_ms_by_config": {k: round(t, 4) for k, t in t_plains.items()}, "plain_config": best,
            "plain_ms": round(t_plain, 4), "batched_graph_ms": round(t_batch, 4),
            "speedup": round(t_plain / t_batch, 4), "plain_graph_ms": round(t_plain_graph, 4),

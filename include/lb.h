@@ -323,6 +323,54 @@ typedef struct lb_tune_result_t {
 lb_status_t lb_autotune(const int32_t* tile_offsets, int32_t num_tiles, int32_t num_atoms, const int32_t* col_idx,
                         const float* vals, const float* x, float* y, const lb_tune_opts_t* opts,
                         lb_tune_result_t* result, lb_plan_t* out_plan, void* stream);
+/*
+ * Measured choice of the batched launch's schedule and tile size (no
+ * counterpart in the paper: its persistent-kernel form, Sec. 5.1, leaves the
+ * configuration to the programmer).  Candidates, in this order (the first,
+ * the library's default batch plan, wins ties): warp workers on waves of
+ * whole matrices at items_per_thread 8 and 4; the look-back shares
+ * (mp_variant 3) at 4 and 8, and at 4 with two-tile shares; warp workers at 4
+ * with 4 dynamic work units per CTA; warp workers at 8 with the whole batch in
+ * one wave.  Each is planned (lb_batch_plan, and lb_batch_prepare_backward
+ * when a backward pass is timed), run once untimed, then timed `opts->reps`
+ * times (default 5; cold L2 with opts->cold_l2) with CUDA events on `stream`
+ * over the passes selected by `passes` (bits LB_TUNE_PASS_FWD: y_cat =
+ * A x_cat; LB_TUNE_PASS_DX: dx_cat = A^T dy_cat; LB_TUNE_PASS_DVALS: dvals_cat);
+ * the fastest median wins.  Arguments as lb_batch_plan / lb_batch_spmv /
+ * lb_batch_spmv_backward (device buffers, caller-owned; the ones a selected
+ * pass needs must not be NULL).  On return the outputs of the selected passes
+ * hold the winner's results, *result the table (host), and *out_plan (if not
+ * NULL) the winner's plan (the caller destroys it).  The cache is shared with
+ * lb_autotune (same clearing, saving, loading and LB_AUTOTUNE_CACHE file),
+ * keyed by the GPU, sizes, passes, cold-L2 flag and a fingerprint of rp_cat
+ * and 4096 col_cat entries; a hit skips the timing.  opts->num_cols and
+ * opts->families are ignored.  Allocates and synchronises `stream`.  Errors:
+ * LB_ERR_INVALID_ARG, LB_ERR_UNSUPPORTED (totals of 2^31 rows or columns),
+ * LB_ERR_CUDA, LB_ERR_OOM; a candidate that fails is recorded and skipped.
+ */
+#define LB_TUNE_PASS_FWD 1
+#define LB_TUNE_PASS_DX 2
+#define LB_TUNE_PASS_DVALS 4
+typedef struct lb_batch_tune_candidate_t {
+  lb_plan_opts_t opts;      /* the lb_batch_plan options of this candidate */
+  float ms;                 /* median time of one step (the selected passes) in milliseconds */
+  float gbps;               /* algorithmic bytes of the selected passes / ms */
+  int32_t reps;             /* timed steps */
+  int32_t status;           /* lb_status_t of planning or running it */
+} lb_batch_tune_candidate_t;
+typedef struct lb_batch_tune_result_t {
+  int32_t num_candidates;
+  int32_t best;             /* index of the winner in candidates[] */
+  int32_t from_cache;       /* 1: taken from the cache, nothing was timed */
+  int32_t passes;           /* the passes timed */
+  lb_plan_opts_t best_opts; /* options that rebuild the winner with lb_batch_plan */
+  lb_batch_tune_candidate_t candidates[LB_TUNE_MAX_CANDIDATES];
+} lb_batch_tune_result_t;
+lb_status_t lb_batch_autotune(int32_t num_mats, const int32_t* host_rows, const int32_t* host_cols,
+                              const int64_t* host_nnz, const int32_t* rp_cat, const int32_t* col_cat,
+                              const float* vals_cat, const float* x_cat, float* y_cat, const float* dy_cat,
+                              float* dx_cat, float* dvals_cat, int32_t passes, const lb_tune_opts_t* opts,
+                              lb_batch_tune_result_t* result, lb_plan_t* out_plan, void* stream);
 /* Empties the autotuner's process-wide cache (in memory; files are not touched). */
 void lb_autotune_cache_clear(void);
 /* Entries in the process-wide cache. */

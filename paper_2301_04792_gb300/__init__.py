@@ -9,9 +9,9 @@ differentiable backward and a batched persistent form.  The compute lives in
 """
 from .buildlib import build  # noqa: F401
 from .lb import (BatchPlan, LBBatchSpMV, LBSpMV, Plan, Schedule, autotune, autotune_cache_clear,  # noqa: F401
-                 autotune_cache_load, autotune_cache_save, autotune_cache_size, batch_spmv, coo_to_csr, csc_to_csr,
+                 autotune_cache_load, autotune_cache_save, autotune_cache_size, batch_autotune, batch_spmv, coo_to_csr, csc_to_csr,
                  heuristic_schedule, merge_diagonals, spmv, sssp)
 
 __all__ = ["build", "Plan", "BatchPlan", "Schedule", "LBSpMV", "LBBatchSpMV", "spmv", "batch_spmv",
            "heuristic_schedule", "merge_diagonals", "autotune", "autotune_cache_clear", "autotune_cache_save",
-           "autotune_cache_load", "autotune_cache_size", "sssp", "coo_to_csr", "csc_to_csr"]
+           "autotune_cache_load", "autotune_cache_size", "batch_autotune", "sssp", "coo_to_csr", "csc_to_csr"]

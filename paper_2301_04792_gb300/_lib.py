@@ -66,6 +66,19 @@ class TuneResult(ctypes.Structure):
                 ("candidates", TuneCandidate * TUNE_MAX_CANDIDATES)]
 
 
+class BatchTuneCandidate(ctypes.Structure):
+    _fields_ = [("opts", PlanOpts), ("ms", ctypes.c_float), ("gbps", ctypes.c_float), ("reps", ctypes.c_int32),
+                ("status", ctypes.c_int32)]
+
+
+class BatchTuneResult(ctypes.Structure):
+    _fields_ = [("num_candidates", ctypes.c_int32), ("best", ctypes.c_int32), ("from_cache", ctypes.c_int32),
+                ("passes", ctypes.c_int32), ("best_opts", PlanOpts),
+                ("candidates", BatchTuneCandidate * TUNE_MAX_CANDIDATES)]
+
+
+TUNE_PASS_FWD, TUNE_PASS_DX, TUNE_PASS_DVALS = 1, 2, 4
+
 # name -> (restype, argtypes); the declarations of include/lb.h
 VP, I32, I64, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
 PLANP = ctypes.POINTER(ctypes.c_void_p)
@@ -84,6 +97,8 @@ SIGNATURES = {
     "lb_status": (I32, [VP, VP]),
     "lb_autotune": (I32, [VP, I32, I32, VP, VP, VP, VP, ctypes.POINTER(TuneOpts), ctypes.POINTER(TuneResult), PLANP,
                           VP]),
+    "lb_batch_autotune": (I32, [I32, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, I32, ctypes.POINTER(TuneOpts),
+                                ctypes.POINTER(BatchTuneResult), PLANP, VP]),
     "lb_autotune_cache_clear": (None, []),
     "lb_autotune_cache_size": (I32, []),
     "lb_autotune_cache_save": (I32, [ctypes.c_char_p]),

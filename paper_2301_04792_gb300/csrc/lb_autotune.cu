@@ -65,6 +65,12 @@ std::string device_ident(int dev) {
          std::to_string(pr.minor);
 }
 
+// Batch cache key: the GPU, number of matrices, total rows / columns / atoms,
+// fingerprint of the concatenated row offsets and a column sample, passes
+// timed and the cold-L2 flag.
+using BKey = std::tuple<std::string, int32_t, int32_t, int32_t, int64_t, uint64_t, int32_t, int32_t>;
+std::map<BKey, lb_batch_tune_result_t> g_bcache;
+
 // ---- persisted cache: one JSON object per line, written and read only here --
 //
 // {"format":"lb_autotune_cache","version":V,"device":"NAME/SMS/CC","rows":R,"atoms":N,"cols":C,
@@ -195,6 +201,80 @@ bool parse_entry(const std::string& line, Key& k, lb_tune_result_t& r) {
   return true;
 }
 
+// Batch entries: {"format":"lb_batch_autotune_cache","version":V,"device":"...","mats":M,"rows":R,
+//  "cols":C,"atoms":N,"fingerprint":"0x...","passes":P,"cold_l2":0|1,"best":b,"best_opts":[12 ints],
+//  "candidates":[[12 ints of options,status,reps,ms,gbps],...]}
+std::string bentry_line(const BKey& k, const lb_batch_tune_result_t& r) {
+  std::string out;
+  char buf[512];
+  std::string dev = std::get<0>(k);
+  for (char& ch : dev)
+    if (ch == '"' || ch == '\\' || (unsigned char)ch < 0x20) ch = '_';
+  std::snprintf(buf, sizeof(buf),
+                "{\"format\":\"lb_batch_autotune_cache\",\"version\":%d,\"device\":\"%s\",\"mats\":%d,"
+                "\"rows\":%d,\"cols\":%d,\"atoms\":%lld,\"fingerprint\":\"0x%016llx\",\"passes\":%d,"
+                "\"cold_l2\":%d,\"best\":%d,\"best_opts\":[",
+                (int)lb_version(), dev.c_str(), std::get<1>(k), std::get<2>(k), std::get<3>(k),
+                (long long)std::get<4>(k), (unsigned long long)std::get<5>(k), std::get<6>(k), std::get<7>(k),
+                r.best);
+  out += buf;
+  const int32_t* o = reinterpret_cast<const int32_t*>(&r.best_opts);
+  for (int i = 0; i < kOptsInts; ++i) {
+    std::snprintf(buf, sizeof(buf), "%s%d", i ? "," : "", o[i]);
+    out += buf;
+  }
+  out += "],\"candidates\":[";
+  for (int i = 0; i < r.num_candidates; ++i) {
+    const lb_batch_tune_candidate_t& c = r.candidates[i];
+    out += i ? ",[" : "[";
+    const int32_t* co = reinterpret_cast<const int32_t*>(&c.opts);
+    for (int q = 0; q < kOptsInts; ++q) {
+      std::snprintf(buf, sizeof(buf), "%d,", co[q]);
+      out += buf;
+    }
+    std::snprintf(buf, sizeof(buf), "%d,%d,%.9g,%.9g]", c.status, c.reps, (double)c.ms, (double)c.gbps);
+    out += buf;
+  }
+  out += "]}\n";
+  return out;
+}
+
+bool parse_bentry(const std::string& line, BKey& k, lb_batch_tune_result_t& r) {
+  long long ver, mats, rows, cols, atoms, passes, cold, best;
+  std::string dev, fps, fmt;
+  std::vector<double> opts, cands;
+  constexpr int kStride = kOptsInts + 4;
+  if (!field_str(line, "format", fmt) || fmt != "lb_batch_autotune_cache" || !field_ll(line, "version", ver) ||
+      ver != lb_version() || !field_str(line, "device", dev) || !field_ll(line, "mats", mats) ||
+      !field_ll(line, "rows", rows) || !field_ll(line, "cols", cols) || !field_ll(line, "atoms", atoms) ||
+      !field_str(line, "fingerprint", fps) || !field_ll(line, "passes", passes) ||
+      !field_ll(line, "cold_l2", cold) || !field_ll(line, "best", best) || !field_nums(line, "best_opts", opts) ||
+      !field_nums(line, "candidates", cands))
+    return false;
+  if ((int)opts.size() != kOptsInts || cands.empty() || cands.size() % kStride != 0 ||
+      cands.size() / kStride > LB_TUNE_MAX_CANDIDATES || best < 0 || best >= (long long)(cands.size() / kStride))
+    return false;
+  std::memset(&r, 0, sizeof(r));
+  r.num_candidates = (int32_t)(cands.size() / kStride);
+  r.best = (int32_t)best;
+  r.passes = (int32_t)passes;
+  int32_t* o = reinterpret_cast<int32_t*>(&r.best_opts);
+  for (int i = 0; i < kOptsInts; ++i) o[i] = (int32_t)opts[i];
+  for (int i = 0; i < r.num_candidates; ++i) {
+    const double* c = cands.data() + kStride * i;
+    lb_batch_tune_candidate_t& t = r.candidates[i];
+    int32_t* co = reinterpret_cast<int32_t*>(&t.opts);
+    for (int q = 0; q < kOptsInts; ++q) co[q] = (int32_t)c[q];
+    t.status = (int32_t)c[kOptsInts];
+    t.reps = (int32_t)c[kOptsInts + 1];
+    t.ms = (float)c[kOptsInts + 2];
+    t.gbps = (float)c[kOptsInts + 3];
+  }
+  const uint64_t fp = std::strtoull(fps.c_str(), nullptr, 16);
+  k = BKey{dev, (int32_t)mats, (int32_t)rows, (int32_t)cols, (int64_t)atoms, fp, (int32_t)passes, (int32_t)cold};
+  return true;
+}
+
 // caller holds g_cache_mu
 lb_status_t load_locked(const char* path, int32_t* loaded) {
   if (loaded) *loaded = 0;
@@ -213,8 +293,13 @@ lb_status_t load_locked(const char* path, int32_t* loaded) {
     }
     Key k;
     lb_tune_result_t r;
+    BKey bk;
+    lb_batch_tune_result_t br;
     if (parse_entry(line, k, r)) {
       g_cache[k] = r;
+      ++n;
+    } else if (parse_bentry(line, bk, br)) {
+      g_bcache[bk] = br;
       ++n;
     }
     line.clear();
@@ -235,6 +320,10 @@ lb_status_t save_locked(const char* path) {
   bool ok = true;
   for (const auto& kv : g_cache) {
     const std::string l = entry_line(kv.first, kv.second);
+    ok = ok && std::fwrite(l.data(), 1, l.size(), f) == l.size();
+  }
+  for (const auto& kv : g_bcache) {
+    const std::string l = bentry_line(kv.first, kv.second);
     ok = ok && std::fwrite(l.data(), 1, l.size(), f) == l.size();
   }
   ok = (std::fclose(f) == 0) && ok;
@@ -360,6 +449,53 @@ lb_status_t run_candidate(const Candidate& c, const int32_t* rp, int32_t R, int3
   return LB_OK;
 }
 
+// Fingerprint of a tile set (its R + 1 offsets) and of 4096 evenly spaced
+// column indices, on the device; synchronises s.
+lb_status_t fingerprint(const int32_t* rp, int32_t R, const int32_t* ci, int64_t N, cudaStream_t s, uint64_t* out) {
+  unsigned long long* d_fp = nullptr;
+  LB_CUDA_TRY(cudaMalloc(&d_fp, sizeof(unsigned long long)));
+  const int32_t samples = N > 0 ? (int32_t)std::min<int64_t>(4096, N) : 0;
+  const int64_t stride = samples > 0 ? std::max<int64_t>(1, N / samples) : 1;
+  const int64_t work = std::max<int64_t>((int64_t)R + 1, samples);
+  const unsigned blocks = (unsigned)std::min<int64_t>((work + 255) / 256, 4096);
+  cudaError_t e = cudaMemsetAsync(d_fp, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) {
+    fingerprint_kernel<<<blocks, 256, 0, s>>>(rp, R, ci, N, stride, samples, d_fp);
+    e = cudaGetLastError();
+  }
+  unsigned long long h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_fp, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_fp);
+  LB_CUDA_TRY(e);
+  *out = h;
+  return LB_OK;
+}
+
+// Batch candidates: the library's default batch plan first (it wins ties),
+// then warp workers at items_per_thread 4, the look-back shares at 4 and 8
+// (4 with two-tile shares), one wave for the whole batch, and dynamic units.
+std::vector<lb_plan_opts_t> batch_candidates() {
+  std::vector<lb_plan_opts_t> v;
+  auto add = [&](int ipt, int variant, int tps, int units, int wave_items) {
+    lb_plan_opts_t o{};
+    o.items_per_thread = ipt;
+    o.mp_variant = variant;
+    o.tiles_per_share = tps;
+    o.units_per_cta = units;
+    o.wave_items = wave_items;
+    v.push_back(o);
+  };
+  add(8, 0, 0, 0, 0);
+  add(4, 0, 0, 0, 0);
+  add(4, 3, 0, 0, 0);
+  add(8, 3, 0, 0, 0);
+  add(4, 3, 2, 0, 0);
+  add(4, 0, 0, 4, 0);
+  add(8, 0, 0, 0, 1 << 30);
+  return v;
+}
+
 }  // namespace
 
 extern "C" {
@@ -367,11 +503,12 @@ extern "C" {
 void lb_autotune_cache_clear(void) {
   std::lock_guard<std::mutex> lock(g_cache_mu);
   g_cache.clear();
+  g_bcache.clear();
 }
 
 int32_t lb_autotune_cache_size(void) {
   std::lock_guard<std::mutex> lock(g_cache_mu);
-  return (int32_t)g_cache.size();
+  return (int32_t)(g_cache.size() + g_bcache.size());
 }
 
 lb_status_t lb_autotune_cache_save(const char* path) {
@@ -426,25 +563,7 @@ lb_status_t lb_autotune(const int32_t* tile_offsets, int32_t num_tiles, int32_t 
   // fingerprint for the cache
   uint64_t fp = 0;
   const bool use_cache = !opts->no_cache && num_tiles > 0;
-  if (use_cache) {
-    unsigned long long* d_fp = nullptr;
-    LB_CUDA_TRY(cudaMalloc(&d_fp, sizeof(unsigned long long)));
-    const int32_t samples = num_atoms > 0 ? (int32_t)std::min<int64_t>(4096, num_atoms) : 0;
-    const int64_t stride = samples > 0 ? std::max<int64_t>(1, num_atoms / samples) : 1;
-    const int64_t work = std::max<int64_t>((int64_t)num_tiles + 1, samples);
-    const unsigned blocks = (unsigned)std::min<int64_t>((work + 255) / 256, 4096);
-    cudaError_t e = cudaMemsetAsync(d_fp, 0, sizeof(unsigned long long), s);
-    if (e == cudaSuccess) {
-      fingerprint_kernel<<<blocks, 256, 0, s>>>(tile_offsets, num_tiles, col_idx, num_atoms, stride, samples, d_fp);
-      e = cudaGetLastError();
-    }
-    unsigned long long h = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_fp, sizeof(h), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFree(d_fp);
-    LB_CUDA_TRY(e);
-    fp = h;
-  }
+  if (use_cache) LB_TRY(fingerprint(tile_offsets, num_tiles, col_idx, num_atoms, s, &fp));
   const Key key{use_cache ? device_ident(dev) : std::string(), num_tiles, num_atoms, C, fp, families,
                 opts->cold_l2 ? 1 : 0};
   bool hit = false;
@@ -524,6 +643,144 @@ lb_status_t lb_autotune(const int32_t* tile_offsets, int32_t num_tiles, int32_t 
   lb_status_t st = lb_spmv(p, col_idx, vals, x, y, s);
   if (st == LB_OK && cudaStreamSynchronize(s) != cudaSuccess) {
     set_error("lb_autotune: final launch failed");
+    st = LB_ERR_CUDA;
+  }
+  if (st != LB_OK || !out_plan) {
+    lb_plan_destroy(p);
+  } else {
+    *out_plan = p;
+  }
+  return st;
+}
+
+lb_status_t lb_batch_autotune(int32_t num_mats, const int32_t* host_rows, const int32_t* host_cols,
+                              const int64_t* host_nnz, const int32_t* rp_cat, const int32_t* col_cat,
+                              const float* vals_cat, const float* x_cat, float* y_cat, const float* dy_cat,
+                              float* dx_cat, float* dvals_cat, int32_t passes, const lb_tune_opts_t* opts,
+                              lb_batch_tune_result_t* result, lb_plan_t* out_plan, void* stream) {
+  if (out_plan) *out_plan = nullptr;
+  if (!result || !opts || num_mats < 1 || !host_rows || !host_cols || !host_nnz || !rp_cat || passes < 1 ||
+      passes > (LB_TUNE_PASS_FWD | LB_TUNE_PASS_DX | LB_TUNE_PASS_DVALS) || opts->reps < 0) {
+    set_error("lb_batch_autotune: need result, opts, num_mats >= 1, the size arrays, rp_cat and passes in 1..7");
+    return LB_ERR_INVALID_ARG;
+  }
+  std::memset(result, 0, sizeof(*result));
+  int64_t R = 0, C = 0, N = 0;
+  for (int m = 0; m < num_mats; ++m) {
+    if (host_rows[m] < 0 || host_cols[m] < 0 || host_nnz[m] < 0) {
+      set_error("lb_batch_autotune: negative size");
+      return LB_ERR_INVALID_ARG;
+    }
+    R += host_rows[m];
+    C += host_cols[m];
+    N += host_nnz[m];
+  }
+  const bool fwd = passes & LB_TUNE_PASS_FWD, dx = passes & LB_TUNE_PASS_DX, dv = passes & LB_TUNE_PASS_DVALS;
+  if ((fwd && !y_cat) || ((dx || dv) && !dy_cat) || (dx && !dx_cat) || (dv && !dvals_cat) ||
+      (N > 0 && (!col_cat || !vals_cat || !x_cat))) {
+    set_error("lb_batch_autotune: a buffer the timed passes need is NULL");
+    return LB_ERR_INVALID_ARG;
+  }
+  if (R >= INT32_MAX || C >= INT32_MAX) {
+    set_error("lb_batch_autotune: batch totals must stay below 2^31 rows and columns");
+    return LB_ERR_UNSUPPORTED;
+  }
+  const int reps = opts->reps ? opts->reps : 5;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0;
+  LB_CUDA_TRY(cudaGetDevice(&dev));
+  const bool use_cache = !opts->no_cache;
+  uint64_t fp = 0;
+  if (use_cache) LB_TRY(fingerprint(rp_cat, (int32_t)(R + num_mats - 1), col_cat, N, s, &fp));
+  const BKey key{use_cache ? device_ident(dev) : std::string(), num_mats, (int32_t)R, (int32_t)C, N, fp, passes,
+                 opts->cold_l2 ? 1 : 0};
+  bool hit = false;
+  if (use_cache) {
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    env_load_locked();
+    auto it = g_bcache.find(key);
+    if (it != g_bcache.end()) {
+      *result = it->second;
+      result->from_cache = 1;
+      hit = true;
+    }
+  }
+  // one step of the timed passes with plan p
+  auto step = [&](lb_plan_t p) -> lb_status_t {
+    if (fwd) LB_TRY(lb_batch_spmv(p, col_cat, vals_cat, x_cat, y_cat, s));
+    if (dx || dv)
+      LB_TRY(lb_batch_spmv_backward(p, col_cat, vals_cat, x_cat, dy_cat, dx ? dx_cat : nullptr,
+                                    dv ? dvals_cat : nullptr, s));
+    return LB_OK;
+  };
+  if (!hit) {
+    Timer t;
+    t.s = s;
+    LB_TRY(t.init(opts->cold_l2 != 0, dev));
+    double bytes = 0.0;
+    if (fwd) bytes += 8.0 * N + 4.0 * (R + num_mats) + 4.0 * C + 4.0 * R;
+    if (dx) bytes += 12.0 * N + 4.0 * (C + num_mats) + 4.0 * R + 4.0 * C;
+    if (dv) bytes += 8.0 * N + 4.0 * (R + num_mats) + 4.0 * R + 4.0 * C;
+    const std::vector<lb_plan_opts_t> cands = batch_candidates();
+    const int n = (int)std::min<size_t>(cands.size(), LB_TUNE_MAX_CANDIDATES);
+    int best = -1;
+    float best_ms = 0.f;
+    for (int i = 0; i < n; ++i) {
+      lb_batch_tune_candidate_t& r = result->candidates[i];
+      r.opts = cands[i];
+      lb_plan_t p = nullptr;
+      lb_status_t st = lb_batch_plan(&p, num_mats, host_rows, host_cols, host_nnz, rp_cat, &cands[i], s);
+      if (st == LB_OK && (dx || dv) && N > 0) st = lb_batch_prepare_backward(p, col_cat, s);
+      if (st == LB_OK) st = step(p);  // untimed: first-use costs
+      std::vector<float> ms;
+      for (int q = 0; st == LB_OK && q < reps; ++q) {
+        if (t.flush) {
+          if (cudaMemsetAsync(t.flush, ++t.flush_round & 0xff, t.flush_bytes, s) != cudaSuccess) st = LB_ERR_CUDA;
+        }
+        if (st == LB_OK && cudaEventRecord(t.e0, s) != cudaSuccess) st = LB_ERR_CUDA;
+        if (st == LB_OK) st = step(p);
+        if (st == LB_OK && (cudaEventRecord(t.e1, s) != cudaSuccess || cudaEventSynchronize(t.e1) != cudaSuccess))
+          st = LB_ERR_CUDA;
+        float m = 0.f;
+        if (st == LB_OK && cudaEventElapsedTime(&m, t.e0, t.e1) != cudaSuccess) st = LB_ERR_CUDA;
+        if (st == LB_OK) ms.push_back(m);
+      }
+      if (p) lb_plan_destroy(p);
+      r.status = st;
+      if (st != LB_OK) {
+        if (cudaPeekAtLastError() != cudaSuccess && cudaDeviceSynchronize() != cudaSuccess) return LB_ERR_CUDA;
+        continue;
+      }
+      std::sort(ms.begin(), ms.end());
+      r.ms = ms[ms.size() / 2];
+      r.reps = (int32_t)ms.size();
+      r.gbps = r.ms > 0.f ? (float)(bytes / (r.ms * 1e-3) / 1e9) : 0.f;
+      if (best < 0 || r.ms < best_ms) {
+        best = i;
+        best_ms = r.ms;
+      }
+    }
+    if (best < 0) {
+      set_error("lb_batch_autotune: no candidate ran");
+      return LB_ERR_CUDA;
+    }
+    result->num_candidates = n;
+    result->best = best;
+    result->passes = passes;
+    result->best_opts = cands[best];
+    if (use_cache) {
+      std::lock_guard<std::mutex> lock(g_cache_mu);
+      g_bcache[key] = *result;
+      if (const char* path = env_cache_path()) save_locked(path);
+    }
+  }
+  // the winner's plan; the outputs of the timed passes by it
+  lb_plan_t p = nullptr;
+  LB_TRY(lb_batch_plan(&p, num_mats, host_rows, host_cols, host_nnz, rp_cat, &result->best_opts, s));
+  lb_status_t st = ((dx || dv) && N > 0) ? lb_batch_prepare_backward(p, col_cat, s) : LB_OK;
+  if (st == LB_OK) st = step(p);
+  if (st == LB_OK && cudaStreamSynchronize(s) != cudaSuccess) {
+    set_error("lb_batch_autotune: final launch failed");
     st = LB_ERR_CUDA;
   }
   if (st != LB_OK || !out_plan) {

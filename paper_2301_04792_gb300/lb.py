@@ -14,7 +14,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import PlanInfo, PlanOpts, TuneOpts, TuneResult, check
+from ._lib import BatchTuneResult, PlanInfo, PlanOpts, TuneOpts, TuneResult, check
 
 
 class Schedule(IntEnum):
@@ -380,6 +380,21 @@ class BatchPlan:
                                       ctypes.c_void_p(_stream(stream))), "lb_batch_plan")
         self._h = h
 
+    @classmethod
+    def _adopt(cls, handle: ctypes.c_void_p, rows, cols, nnz, rp_cat: torch.Tensor) -> "BatchPlan":
+        """Wraps a batch plan handle made by the library (the batch autotuner's winner)."""
+        self = cls.__new__(cls)
+        self._lib = _lib.load()
+        self.rows = np.ascontiguousarray(rows, dtype=np.int32)
+        self.cols = np.ascontiguousarray(cols, dtype=np.int32)
+        self.nnz = np.ascontiguousarray(nnz, dtype=np.int64)
+        self.rp_cat = rp_cat
+        self.total_rows = int(self.rows.sum())
+        self.total_cols = int(self.cols.sum())
+        self.total_nnz = int(self.nnz.sum())
+        self._h = handle
+        return self
+
     @property
     def handle(self):
         if self._h is None:
@@ -437,6 +452,68 @@ class BatchPlan:
             out = torch.empty(self.total_nnz, dtype=torch.int32, device=self.rp_cat.device)
         check(self._lib.lb_atom_tiles(self.handle, _ptr(out), ctypes.c_void_p(_stream(stream))), "lb_atom_tiles")
         return out
+
+
+def _batch_candidate_name(o) -> str:
+    s = f"batch_ipt{o.items_per_thread}_v{o.mp_variant}"
+    if o.tiles_per_share > 1:
+        s += f"_tps{o.tiles_per_share}"
+    if o.units_per_cta > 1:
+        s += f"_u{o.units_per_cta}"
+    if o.wave_items:
+        s += f"_wave{o.wave_items}"
+    return s
+
+
+def batch_autotune(rows, cols, nnz, rp_cat: torch.Tensor, col_cat: torch.Tensor, vals_cat: torch.Tensor,
+                   x_cat: torch.Tensor, dy_cat: torch.Tensor | None = None, passes: str = "fwd", y_cat=None,
+                   dx_cat=None, dvals_cat=None, reps: int = 0, cold_l2: bool = False, use_cache: bool = True,
+                   stream=None):
+    """Times the batch plan candidates (``lb_batch_autotune``) over the passes named in
+    ``passes`` ("fwd", "dx", "dvals" joined by "+", e.g. "fwd+dx+dvals") and returns
+    ``(plan, report)``: the winner's BatchPlan and a dict with the timed table and the
+    outputs of the timed passes by the winner."""
+    lib = _lib.load()
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    cols = np.ascontiguousarray(cols, dtype=np.int32)
+    nnz = np.ascontiguousarray(nnz, dtype=np.int64)
+    R, C, N = int(rows.sum()), int(cols.sum()), int(nnz.sum())
+    bits = {"fwd": _lib.TUNE_PASS_FWD, "dx": _lib.TUNE_PASS_DX, "dvals": _lib.TUNE_PASS_DVALS}
+    mask = 0
+    for part in str(passes).split("+"):
+        mask |= bits[part.strip()]
+    _need(rp_cat, torch.int32, "rp_cat", R + rows.shape[0])
+    _need(col_cat, torch.int32, "col_cat", N)
+    _need(vals_cat, torch.float32, "vals_cat", N)
+    _need(x_cat, torch.float32, "x_cat", C)
+    dev = x_cat.device
+    if mask & _lib.TUNE_PASS_FWD and y_cat is None:
+        y_cat = torch.empty(R, dtype=torch.float32, device=dev)
+    if mask & (_lib.TUNE_PASS_DX | _lib.TUNE_PASS_DVALS):
+        _need(dy_cat, torch.float32, "dy_cat", R)
+    if mask & _lib.TUNE_PASS_DX and dx_cat is None:
+        dx_cat = torch.empty(C, dtype=torch.float32, device=dev)
+    if mask & _lib.TUNE_PASS_DVALS and dvals_cat is None:
+        dvals_cat = torch.empty(N, dtype=torch.float32, device=dev)
+    o = TuneOpts(reps=int(reps), cold_l2=int(bool(cold_l2)), no_cache=int(not use_cache))
+    res = BatchTuneResult()
+    h = ctypes.c_void_p()
+    check(lib.lb_batch_autotune(rows.shape[0], rows.ctypes.data_as(ctypes.c_void_p),
+                                cols.ctypes.data_as(ctypes.c_void_p), nnz.ctypes.data_as(ctypes.c_void_p),
+                                _ptr(rp_cat), _ptr(col_cat), _ptr(vals_cat), _ptr(x_cat), _ptr(y_cat), _ptr(dy_cat),
+                                _ptr(dx_cat), _ptr(dvals_cat), mask, ctypes.byref(o), ctypes.byref(res),
+                                ctypes.byref(h), ctypes.c_void_p(_stream(stream))), "lb_batch_autotune")
+    cands = []
+    for i in range(res.num_candidates):
+        c = res.candidates[i]
+        cands.append({"name": _batch_candidate_name(c.opts), "ms": c.ms, "gbps": c.gbps, "reps": c.reps,
+                      "status": c.status,
+                      "opts": {f: getattr(c.opts, f) for f, _ in PlanOpts._fields_ if f != "reserved"}})
+    report = {"candidates": cands, "best": cands[res.best]["name"], "from_cache": bool(res.from_cache),
+              "passes": passes, "best_opts": {f: getattr(res.best_opts, f) for f, _ in PlanOpts._fields_
+                                              if f != "reserved"},
+              "y": y_cat, "dx": dx_cat, "dvals": dvals_cat}
+    return BatchPlan._adopt(h, rows, cols, nnz, rp_cat), report
 
 
 class LBSpMV(torch.autograd.Function):

@@ -163,3 +163,18 @@ def test_autotune_cache_file_round_trip(lib, tmp_path):
     lib.lb_autotune_cache_clear()
     assert lib.lb_autotune_cache_load(str(tmp_path / "missing.jsonl").encode(), None) == 1
     assert lib.lb_autotune_cache_save(b"") == 1
+
+
+def test_batch_autotune_rejects_bad_arguments(lib):
+    """Argument checks of lb_batch_autotune run on the host, before any launch."""
+    res = _lib.BatchTuneResult()
+    opts = _lib.TuneOpts()
+    rows = (ctypes.c_int32 * 1)(10)
+    nnz = (ctypes.c_int64 * 1)(20)
+    fake = ctypes.c_void_p(16)
+    args = [1, rows, rows, nnz, fake, fake, fake, fake, fake, None, None, None]
+    # passes out of range, no result, num_mats 0, dy missing for a backward pass
+    assert lib.lb_batch_autotune(*args, 0, ctypes.byref(opts), ctypes.byref(res), None, None) == 1
+    assert lib.lb_batch_autotune(*args, 1, ctypes.byref(opts), None, None, None) == 1
+    assert lib.lb_batch_autotune(0, *args[1:], 1, ctypes.byref(opts), ctypes.byref(res), None, None) == 1
+    assert lib.lb_batch_autotune(*args, 3, ctypes.byref(opts), ctypes.byref(res), None, None) == 1

@@ -188,3 +188,38 @@ def test_full_differentiable_batch_64(lbmod):
             assert_within_bound(y[rb[mi]:rb[mi + 1]], y64, yb, f"diff y m{mi} {name}")
             assert_within_bound(dx[cb[mi]:cb[mi + 1]], dx64, dxb, f"diff dx m{mi} {name}")
             assert np.array_equal(dvals[nb[mi]:nb[mi + 1]].view(np.uint32), dv32.view(np.uint32)), (mi, name)
+
+
+def test_batch_autotune_fwd_bwd_matches_oracle(lbmod):
+    """lb_batch_autotune times every batch candidate over fwd + dx + dvals, picks the
+    fastest, and the winner's outputs and plan agree with the oracle; a second call
+    is a cache hit with the same choice."""
+    import torch
+    b = W.batch(num=40, rmin=50, rmax=5000, mmin=1, mmax=64, seed=3)
+    xs, dys = batch_inputs(b)
+    y64, yb, dx64, dxb, dv32 = oracle_batch(b, xs, dys)
+    rp_cat, ci, v, xd, dyd = to_dev(b.rp_cat(), b.ci_cat(), b.v_cat(), np.concatenate(xs), np.concatenate(dys))
+    lbmod.autotune_cache_clear()
+    plan, rep = lbmod.batch_autotune(b.rows(), b.cols(), b.nnz(), rp_cat, ci, v, xd, dyd, passes="fwd+dx+dvals",
+                                     reps=3)
+    cands = rep["candidates"]
+    assert len(cands) == 7 and all(c["status"] == 0 and c["ms"] > 0 for c in cands), cands
+    best_ms = min(c["ms"] for c in cands)
+    assert rep["best"] == next(c["name"] for c in cands if c["ms"] == best_ms)
+    assert not rep["from_cache"]
+    assert_within_bound(rep["y"].cpu().numpy(), y64, yb, "tuned batch y")
+    assert_within_bound(rep["dx"].cpu().numpy(), dx64, dxb, "tuned batch dx")
+    assert np.array_equal(rep["dvals"].cpu().numpy().view(np.uint32), dv32.view(np.uint32))
+    # the returned plan is the winner and runs on its own
+    assert plan.info()["mp_variant"] == rep["best_opts"]["mp_variant"]
+    y = plan.spmv(ci, v, xd)
+    assert torch.equal(y.view(torch.int32), rep["y"].view(torch.int32))
+    _, rep2 = lbmod.batch_autotune(b.rows(), b.cols(), b.nnz(), rp_cat, ci, v, xd, dyd, passes="fwd+dx+dvals",
+                                   reps=3)
+    assert rep2["from_cache"] and rep2["best"] == rep["best"]
+    assert_within_bound(rep2["y"].cpu().numpy(), y64, yb, "cached tuned batch y")
+    # forward only is another key
+    _, rep3 = lbmod.batch_autotune(b.rows(), b.cols(), b.nnz(), rp_cat, ci, v, xd, passes="fwd", reps=2)
+    assert not rep3["from_cache"] and rep3["dx"] is None
+    assert_within_bound(rep3["y"].cpu().numpy(), y64, yb, "fwd-only tuned batch y")
+    lbmod.autotune_cache_clear()
