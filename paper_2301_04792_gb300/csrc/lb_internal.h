@@ -62,6 +62,12 @@ struct MpTable {
   int64_t* share_ent = nullptr;
   int4* share_head = nullptr;
   unsigned long long* records = nullptr;
+  // variant 0: the carries settled run by run (a run = consecutive work units
+  // whose carry names the same row, plus the unit after them that closes it)
+  int2* unit_runs = nullptr;  // per unit: (run it belongs to, run it closes), -1 = none
+  int4* runs = nullptr;       // per run: first unit, last unit, row, participants
+  unsigned* run_cnt = nullptr;
+  int num_runs = 0;
   void release();
 };
 

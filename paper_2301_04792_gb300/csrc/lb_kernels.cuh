@@ -218,6 +218,12 @@ struct MpArgs {
   const int4* share_head;
   unsigned long long* records;
   int* status;
+  // warp kernels: the carries settled run by run (nullptr: the last CTA to
+  // finish combines every carry); a run is a span of consecutive work units
+  // whose carries name the same row, and the unit after it closes that row
+  const int2* unit_runs;    // per work unit: (run it belongs to, run it closes), -1 = none
+  const int4* runs;         // per run: first unit, last unit, row, participants (units + 1)
+  unsigned* run_cnt;        // per run: participants done in this launch (back to 0 by the last)
   // expand kernels
   const float* dy;          // dvals: upstream gradient per tile
   float* dvals;             // dvals output per atom
@@ -1071,6 +1077,29 @@ struct WarpWalker {
   }
 };
 
+// Work unit u of a warp kernel is done: its carry slot is written and every
+// row store of the unit is fenced.  For each run the unit takes part in (as a
+// member, or as the unit that closes the run's row) count it in; the last of
+// the run's participants to arrive adds the run's carries, in unit order, to
+// the row (whose stored value already holds the closing unit's part) and
+// resets the count for the next launch.  Called by one thread.
+__device__ __forceinline__ void settle_unit_runs(const MpArgs& a, int u) {
+  const int2 ur = __ldg(a.unit_runs + u);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int r = k == 0 ? ur.x : ur.y;
+    if (r < 0) continue;
+    const int4 d = __ldg(a.runs + r);
+    if (atomicAdd(a.run_cnt + r, 1u) + 1u != (unsigned)d.w) continue;
+    __threadfence();
+    float sum = 0.f;
+    for (int q = d.x; q <= d.y; ++q) sum += __ldcg(a.carry_val + q);
+    float* py = a.out + d.z;
+    __stcg(py, __ldcg(py) + sum);
+    a.run_cnt[r] = 0u;
+  }
+}
+
 // Merge-path SpMV with warps as the workers and the fix-up of Sec. 5.2.1
 // done inside the launch.  The plan's split table gives every warp worker an
 // equal share of rows + atoms; a WORK UNIT is the 8 consecutive shares of one
@@ -1121,6 +1150,7 @@ __global__ void __launch_bounds__(256, IPT <= 4 ? 5 : IPT <= 8 ? 4 : 2) mp_spmv_
       s_cval[it & 1][warp] = carry;
     }
     if (threadIdx.x == 0) s_unit[it & 1] = dynamic ? (int)gridDim.x + (int)atomicAdd(a.ticket + 1, 1u) : nunits;
+    if (a.runs) __threadfence();  // this warp's row stores, before the unit's runs are counted in
     __syncthreads();
     // a run that a later warp of this CTA closed is added to its row, the run
     // left open by the last warp becomes the unit's carry-out
@@ -1142,8 +1172,21 @@ __global__ void __launch_bounds__(256, IPT <= 4 ? 5 : IPT <= 8 ? 4 : 2) mp_spmv_
         a.carry_row[u] = row;
         a.carry_val[u] = v;
       }
+      if (a.runs) {
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) settle_unit_runs(a, u);
+      }
     }
     u = s_unit[it & 1];
+  }
+  if (a.runs) {
+    // every run is settled by its last participant; the unit counter goes back to 0
+    if (dynamic && cta_ticket(a, &s_last) && threadIdx.x == 0) {
+      a.ticket[0] = 0u;
+      a.ticket[1] = 0u;
+    }
+    return;
   }
   // rows split between units, all waves at once (a wave's rows are never
   // touched by a later wave, and the slots of all waves are in row order)

@@ -21,6 +21,13 @@ void MpTable::release() {
   cudaFree(share_ent);
   cudaFree(share_head);
   cudaFree(records);
+  cudaFree(unit_runs);
+  cudaFree(runs);
+  cudaFree(run_cnt);
+  unit_runs = nullptr;
+  runs = nullptr;
+  run_cnt = nullptr;
+  num_runs = 0;
   share_ent = nullptr;
   share_head = nullptr;
   records = nullptr;
@@ -328,6 +335,27 @@ __global__ void mp_splits_weighted_kernel(const int32_t* __restrict__ rp, int32_
   diag[e] = d;
 }
 
+// Carry row of every work unit of a warp-worker table: the row open at the
+// end of the unit's last share (its 8th warp's), -1 where none may be named
+// (the end of a wave, or of the tile set).
+__global__ void unit_carry_rows_kernel(const int2* __restrict__ splits, const lbk::WaveDesc* __restrict__ waves,
+                                       int num_waves, int workers, int tpc, int32_t R, int32_t* out) {
+  const int upw = workers / 8;
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= num_waves * upw) return;
+  const int v = u / upw, k = u - v * upw;
+  int64_t ebase = 0;
+  int t = tpc;
+  int32_t row_end = R;
+  if (waves) {
+    ebase = waves[v].entry_base;
+    t = waves[v].tpc;
+    row_end = waves[v].row_end;
+  }
+  const int2 e = splits[ebase + (int64_t)(k * 8 + 7) * (t + 1) + t];
+  out[u] = e.x < row_end ? e.x : -1;
+}
+
 __global__ void mp_splits_at_kernel(const int32_t* __restrict__ rp, int32_t R, int64_t N,
                                     const int64_t* __restrict__ diag, int64_t entries, int2* out) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -421,6 +449,56 @@ static lb_status_t build_guided_table(MpTable& t, const int32_t* rp, int32_t R, 
   // the host vectors must outlive the copies
   LB_CUDA_TRY(cudaStreamSynchronize(s));
   t.built = true;
+  return LB_OK;
+}
+
+// Runs of a warp-worker table (variant 0): consecutive work units whose
+// carries name the same row r, followed by the unit that closes r (the unit
+// after a maximal run never carries r itself, so it holds r's end).  Each unit
+// is a member of at most one run and closes at most one.  Synchronises s.
+static lb_status_t build_runs(MpTable& t, int32_t R, cudaStream_t s) {
+  const int upw = t.workers / 8;
+  const int64_t nunits = (int64_t)upw * t.num_waves;
+  if (nunits < 1) return LB_OK;
+  int32_t* d_rows = nullptr;
+  LB_CUDA_TRY(cudaMalloc(&d_rows, sizeof(int32_t) * (size_t)nunits));
+  unit_carry_rows_kernel<<<(unsigned)((nunits + 255) / 256), 256, 0, s>>>(
+      t.splits, t.num_waves > 1 ? static_cast<const lbk::WaveDesc*>(t.d_waves) : nullptr, t.num_waves, t.workers,
+      t.tiles_per_cta, R, d_rows);
+  std::vector<int32_t> rows((size_t)nunits);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(rows.data(), d_rows, sizeof(int32_t) * rows.size(), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_rows);
+  LB_CUDA_TRY(e);
+  std::vector<int2> unit_runs((size_t)nunits, make_int2(-1, -1));
+  std::vector<int4> runs;
+  for (int64_t u = 0; u < nunits;) {
+    if (rows[u] < 0) {
+      ++u;
+      continue;
+    }
+    int64_t b = u;
+    while (b + 1 < nunits && rows[b + 1] == rows[u]) ++b;
+    if (b + 1 >= nunits) {
+      set_error("merge-path: a carry run without a closing unit");
+      return LB_ERR_CUDA;
+    }
+    const int r = (int)runs.size();
+    runs.push_back(make_int4((int)u, (int)b, rows[u], (int)(b - u + 2)));
+    for (int64_t q = u; q <= b; ++q) unit_runs[q].x = r;
+    unit_runs[b + 1].y = r;
+    u = b + 1;
+  }
+  LB_CUDA_TRY(cudaMalloc(&t.unit_runs, sizeof(int2) * unit_runs.size()));
+  LB_CUDA_TRY(cudaMalloc(&t.runs, sizeof(int4) * std::max<size_t>(1, runs.size())));
+  LB_CUDA_TRY(cudaMalloc(&t.run_cnt, sizeof(unsigned) * std::max<size_t>(1, runs.size())));
+  LB_CUDA_TRY(cudaMemcpyAsync(t.unit_runs, unit_runs.data(), sizeof(int2) * unit_runs.size(), cudaMemcpyHostToDevice, s));
+  if (!runs.empty())
+    LB_CUDA_TRY(cudaMemcpyAsync(t.runs, runs.data(), sizeof(int4) * runs.size(), cudaMemcpyHostToDevice, s));
+  LB_CUDA_TRY(cudaMemsetAsync(t.run_cnt, 0, sizeof(unsigned) * std::max<size_t>(1, runs.size()), s));
+  LB_CUDA_TRY(cudaStreamSynchronize(s));  // the host vectors must outlive the copies
+  t.num_runs = (int)runs.size();
   return LB_OK;
 }
 
@@ -557,6 +635,10 @@ lb_status_t build_mp_table(MpTable& t, const int32_t* rp, int32_t R, int64_t N, 
     split_matrix_kernel<<<blocks, threads, 0, s>>>(t.splits, t.entries, batch->nnz_base, batch->num, t.split_m);
     LB_CUDA_TRY(cudaGetLastError());
   }
+  // runs for tables of one static unit per CTA; with dynamic units (several per CTA, or waves) the
+  // per-unit fences and counts cost more than the single fix-up pass of the last CTA (measured on
+  // the power-law matrix with 8 units per CTA: 123 -> 135 us)
+  if (variant == 0 && t.num_waves == 1 && t.workers / 8 == t.grid) LB_TRY(build_runs(t, R, s));
   t.built = true;
   return LB_OK;
 }
@@ -590,6 +672,9 @@ static lbk::MpArgs make_args(const MpTable& t, const SpmvCall& c) {
   a.waves = static_cast<const lbk::WaveDesc*>(t.d_waves);
   a.num_waves = t.num_waves;
   a.status = c.status;
+  a.unit_runs = t.unit_runs;
+  a.runs = t.unit_runs ? t.runs : nullptr;
+  a.run_cnt = t.run_cnt;
   return a;
 }
 
