@@ -107,7 +107,12 @@ typedef struct lb_plan_opts_t {
                                share inside long rows (closing a row costs a warp more than one atom);
                                the tiles inside a share keep items_per_tile items.  0 or 1 = the paper's
                                equal rows + atoms; at most 64; batch plans ignore it */
-  int32_t reserved[1];
+  int32_t staged;           /* LB_THREAD_MAPPED: nonzero = each warp's 32 tiles (one per lane) have
+                               their atoms copied into shared memory with coalesced loads first (when
+                               they fit: up to 864 atoms per warp), and lane k's gathers then walk
+                               tile k there, so that one gather instruction reads entry j of 32
+                               neighbouring tiles (banded and stencil matrices touch one or two
+                               lines of x per instruction); 0 = Listing 3 as printed.  Same sums */
 } lb_plan_opts_t;
 
 /* What a plan resolved to (for tests, the autotuner and reporting). */
@@ -265,7 +270,7 @@ lb_status_t lb_spmv_noalloc(const int32_t* tile_offsets, int32_t num_tiles, int3
  *   LB_TUNE_MP_CTA   merge-path, CTA workers: per-thread search (variant 1) and
  *                    bulk-copy ring (variant 2, only for 16-byte aligned buffers),
  *                    items_per_thread 4 and 8
- *   LB_TUNE_THREAD   thread-mapped
+ *   LB_TUNE_THREAD   thread-mapped, as printed and with the atoms staged in shared memory
  *   LB_TUNE_GROUP    group-mapped with groups of 4, 8, 16, 32 (warp-mapped), 64,
  *                    128 and 256 (block-mapped) threads
  */
@@ -292,6 +297,7 @@ typedef struct lb_tune_candidate_t {
   int32_t mp_variant;       /* merge-path worker variant */
   int32_t units_per_cta;    /* merge-path warp workers: work units per CTA */
   int32_t row_weight;       /* merge-path variant 0: weight of a row end in the shares (1 = unweighted) */
+  int32_t staged;           /* thread-mapped: atoms staged in shared memory (lb_plan_opts_t.staged) */
   float ms;                 /* median time of one lb_spmv in milliseconds (the single time if pruned) */
   float gbps;               /* algorithmic bytes (8 nnz + 4 (rows + 1) + 4 cols + 4 rows) / ms */
   int32_t reps;             /* timed launches */

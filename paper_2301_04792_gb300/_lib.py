@@ -29,7 +29,7 @@ class PlanOpts(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_int32), ("validate", ctypes.c_int32), ("mp_variant", ctypes.c_int32),
                 ("wave_items", ctypes.c_int32), ("units_per_cta", ctypes.c_int32),
                 ("tiles_per_share", ctypes.c_int32), ("items_per_thread_t", ctypes.c_int32),
-                ("row_weight", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("row_weight", ctypes.c_int32), ("staged", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -55,7 +55,7 @@ class TuneOpts(ctypes.Structure):
 class TuneCandidate(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int32), ("items_per_thread", ctypes.c_int32), ("group_size", ctypes.c_int32),
                 ("mp_variant", ctypes.c_int32), ("units_per_cta", ctypes.c_int32), ("row_weight", ctypes.c_int32),
-                ("ms", ctypes.c_float),
+                ("staged", ctypes.c_int32), ("ms", ctypes.c_float),
                 ("gbps", ctypes.c_float),
                 ("reps", ctypes.c_int32), ("status", ctypes.c_int32)]
 

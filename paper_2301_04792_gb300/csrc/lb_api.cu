@@ -1,4 +1,5 @@
 // C ABI: plans, single-matrix SpMV and its backward, status and host helpers.
+#include <algorithm>
 #include <cstring>
 #include <string>
 
@@ -108,7 +109,7 @@ extern "C" {
 
 const char* lb_last_error(void) { return g_last_error.c_str(); }
 
-int32_t lb_version(void) { return 10000; }
+int32_t lb_version(void) { return 10100; }
 
 int32_t lb_probe_gather_grid(void) {
   int dev = 0;
@@ -215,6 +216,7 @@ lb_status_t lb_plan_ex(lb_plan_t* out, const int32_t* tile_offsets, int32_t num_
     schedule = lb_heuristic_schedule(num_tiles, o.num_cols > 0 ? o.num_cols : num_tiles, num_atoms);
   p->schedule = schedule;
   p->group_size = schedule == LB_WARP_MAPPED ? 32 : schedule == LB_BLOCK_MAPPED ? kBlock : o.group_size;
+  if (schedule == LB_THREAD_MAPPED && o.staged) p->tm_grid = tm_staged_grid(p->num_sms);
   if (schedule == LB_GROUP_MAPPED && !pow2_group(p->group_size)) {
     delete p;
     set_error("lb_plan: group_size must be a power of two in [4, 256]");
@@ -309,7 +311,8 @@ lb_status_t lb_plan_get_info(lb_plan_t p, lb_plan_info_t* info) {
       info->kernels_per_spmv = p->mp.items > 0 ? 1 : 0;
       break;
     case LB_THREAD_MAPPED:
-      info->grid = (int32_t)((R + kBlock - 1) / kBlock);
+      info->grid = p->tm_grid ? (int32_t)std::min<int64_t>(((R + 31) / 32 + 7) / 8, p->tm_grid)
+                              : (int32_t)((R + kBlock - 1) / kBlock);
       info->kernels_per_spmv = R > 0 ? 1 : 0;
       break;
     default: {
@@ -355,7 +358,7 @@ lb_status_t lb_spmv(lb_plan_t p, const int32_t* col_idx, const float* vals, cons
   SpmvCall c{p->rp, p->num_tiles, col_idx, vals, nullptr, x, y, p->opts.validate ? p->num_cols : 0, p->d_status};
   switch (p->schedule) {
     case LB_THREAD_MAPPED:
-      return launch_tm_spmv(c, s);
+      return p->tm_grid ? launch_tm_staged_spmv(c, p->tm_grid, s) : launch_tm_spmv(c, s);
     case LB_WARP_MAPPED:
     case LB_BLOCK_MAPPED:
     case LB_GROUP_MAPPED:
@@ -447,7 +450,7 @@ lb_status_t lb_spmv_backward(lb_plan_t p, int32_t num_cols, const int32_t* col_i
       SpmvCall c{p->cp, num_cols, p->riT, vals, p->perm, dy, dx, 0, p->d_status};
       switch (p->schedule) {
         case LB_THREAD_MAPPED:
-          LB_TRY(launch_tm_spmv(c, s));
+          LB_TRY(p->tm_grid ? launch_tm_staged_spmv(c, p->tm_grid, s) : launch_tm_spmv(c, s));
           break;
         case LB_WARP_MAPPED:
         case LB_BLOCK_MAPPED:

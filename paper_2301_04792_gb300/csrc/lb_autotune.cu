@@ -48,6 +48,7 @@ struct Candidate {
   int ipt, group, variant;
   int units = 1;       // merge-path warp workers: work units per CTA
   int row_weight = 1;  // merge-path variant 0: weight of a row end in the shares
+  int staged = 0;      // thread-mapped: atoms staged in shared memory
 };
 
 // Cache key: the GPU (name / SM count / compute capability, so that a cache
@@ -76,7 +77,7 @@ std::map<BKey, lb_batch_tune_result_t> g_bcache;
 // {"format":"lb_autotune_cache","version":V,"device":"NAME/SMS/CC","rows":R,"atoms":N,"cols":C,
 //  "fingerprint":"0x...","families":F,"cold_l2":0|1,"best":b,"heuristic":h,"best_schedule":s,
 //  "best_opts":[12 ints of lb_plan_opts_t],"candidates":[[schedule,ipt,group,variant,units,row_weight,
-//  status,reps,ms,gbps],...]}
+//  staged,status,reps,ms,gbps],...]}
 constexpr int kOptsInts = (int)(sizeof(lb_plan_opts_t) / sizeof(int32_t));
 
 std::string entry_line(const Key& k, const lb_tune_result_t& r) {
@@ -101,9 +102,9 @@ std::string entry_line(const Key& k, const lb_tune_result_t& r) {
   out += "],\"candidates\":[";
   for (int i = 0; i < r.num_candidates; ++i) {
     const lb_tune_candidate_t& c = r.candidates[i];
-    std::snprintf(buf, sizeof(buf), "%s[%d,%d,%d,%d,%d,%d,%d,%d,%.9g,%.9g]", i ? "," : "", c.schedule,
-                  c.items_per_thread, c.group_size, c.mp_variant, c.units_per_cta, c.row_weight, c.status, c.reps,
-                  (double)c.ms, (double)c.gbps);
+    std::snprintf(buf, sizeof(buf), "%s[%d,%d,%d,%d,%d,%d,%d,%d,%d,%.9g,%.9g]", i ? "," : "", c.schedule,
+                  c.items_per_thread, c.group_size, c.mp_variant, c.units_per_cta, c.row_weight, c.staged, c.status,
+                  c.reps, (double)c.ms, (double)c.gbps);
     out += buf;
   }
   out += "]}\n";
@@ -172,18 +173,20 @@ bool parse_entry(const std::string& line, Key& k, lb_tune_result_t& r) {
       !field_ll(line, "heuristic", heur) || !field_ll(line, "best_schedule", bs) ||
       !field_nums(line, "best_opts", opts) || !field_nums(line, "candidates", cands))
     return false;
-  if ((int)opts.size() != kOptsInts || cands.size() % 10 != 0 || cands.size() / 10 > LB_TUNE_MAX_CANDIDATES ||
-      cands.empty() || best < 0 || best >= (long long)(cands.size() / 10) || heur >= (long long)(cands.size() / 10))
+  constexpr size_t kStride = 11;
+  if ((int)opts.size() != kOptsInts || cands.size() % kStride != 0 || cands.size() / kStride > LB_TUNE_MAX_CANDIDATES ||
+      cands.empty() || best < 0 || best >= (long long)(cands.size() / kStride) ||
+      heur >= (long long)(cands.size() / kStride))
     return false;
   std::memset(&r, 0, sizeof(r));
-  r.num_candidates = (int32_t)(cands.size() / 10);
+  r.num_candidates = (int32_t)(cands.size() / kStride);
   r.best = (int32_t)best;
   r.heuristic = (int32_t)heur;
   r.best_schedule = (int32_t)bs;
   int32_t* o = reinterpret_cast<int32_t*>(&r.best_opts);
   for (int i = 0; i < kOptsInts; ++i) o[i] = (int32_t)opts[i];
   for (int i = 0; i < r.num_candidates; ++i) {
-    const double* c = cands.data() + 10 * i;
+    const double* c = cands.data() + kStride * i;
     lb_tune_candidate_t& t = r.candidates[i];
     t.schedule = (int32_t)c[0];
     t.items_per_thread = (int32_t)c[1];
@@ -191,10 +194,11 @@ bool parse_entry(const std::string& line, Key& k, lb_tune_result_t& r) {
     t.mp_variant = (int32_t)c[3];
     t.units_per_cta = (int32_t)c[4];
     t.row_weight = (int32_t)c[5];
-    t.status = (int32_t)c[6];
-    t.reps = (int32_t)c[7];
-    t.ms = (float)c[8];
-    t.gbps = (float)c[9];
+    t.staged = (int32_t)c[6];
+    t.status = (int32_t)c[7];
+    t.reps = (int32_t)c[8];
+    t.ms = (float)c[9];
+    t.gbps = (float)c[10];
   }
   const uint64_t fp = std::strtoull(fps.c_str(), nullptr, 16);
   k = Key{dev, (int32_t)rows, (int32_t)atoms, (int32_t)cols, fp, (int32_t)fam, (int32_t)cold};
@@ -367,6 +371,7 @@ std::vector<Candidate> candidate_list(lb_schedule_t prior, int families, bool al
       for (int ipt : {4, 8}) v.push_back({LB_MERGE_PATH, ipt, 0, 2});
   }
   if (prior != LB_THREAD_MAPPED && (families & LB_TUNE_THREAD)) v.push_back({LB_THREAD_MAPPED, 0, 0, 0});
+  if (families & LB_TUNE_THREAD) v.push_back({LB_THREAD_MAPPED, 0, 0, 0, 1, 1, 1});
   if (families & LB_TUNE_GROUP) {
     for (int g : {4, 8, 16}) v.push_back({LB_GROUP_MAPPED, 0, g, 0});
     v.push_back({LB_WARP_MAPPED, 0, 32, 0});
@@ -384,6 +389,7 @@ lb_plan_opts_t opts_of(const Candidate& c, int32_t num_cols) {
   o.mp_variant = c.variant;
   o.units_per_cta = c.units;
   o.row_weight = c.row_weight;
+  o.staged = c.staged;
   return o;
 }
 
@@ -595,7 +601,8 @@ lb_status_t lb_autotune(const int32_t* tile_offsets, int32_t num_tiles, int32_t 
       r.mp_variant = c.variant;
       r.units_per_cta = c.units;
       r.row_weight = c.row_weight;
-      if ((c.schedule == prior) && heur < 0 &&
+      r.staged = c.staged;
+      if ((c.schedule == prior) && heur < 0 && !c.staged &&
           (c.schedule != LB_MERGE_PATH || (c.ipt == 8 && c.variant == 0 && c.units == 1 && c.row_weight == 1)))
         heur = i;
       if (num_tiles == 0) {

@@ -102,6 +102,7 @@ struct lb_plan_s {
   lb_schedule_t schedule = LB_MERGE_PATH;
   lb_plan_opts_t opts{};
   int group_size = 32;
+  int tm_grid = 0;  // staged thread-mapped schedule: CTAs of one wave
   // tile set (single matrix: caller's offsets; batch: plan-owned global offsets)
   const int32_t* rp = nullptr;
   int32_t num_tiles = 0;
@@ -143,6 +144,8 @@ lb_status_t launch_mp_spmv(const MpTable& t, const SpmvCall& c, cudaStream_t s);
 lb_status_t launch_mp_expand(const MpTable& t, const SpmvCall& c, const float* dy, float* dvals,
                              int32_t* tile_of_atom, cudaStream_t s);
 lb_status_t launch_tm_spmv(const SpmvCall& c, cudaStream_t s);
+lb_status_t launch_tm_staged_spmv(const SpmvCall& c, int grid, cudaStream_t s);
+int tm_staged_grid(int num_sms);
 lb_status_t launch_gm_spmv(int group, const SpmvCall& c, int num_sms, cudaStream_t s);
 
 // transpose (lb_transpose.cu): stable counting sort of atoms by key.

@@ -1608,6 +1608,82 @@ __global__ void __launch_bounds__(BLOCK) tm_spmv_kernel(const int32_t* __restric
   }
 }
 
+// Thread-mapped schedule with the atoms staged in shared memory (Sec. 4.2's
+// thread-mapped loop; the staging is the shared-memory use of Sec. 5.2.3).
+// A warp takes 32 consecutive tiles, one per lane.  When their atoms fit in
+// the warp's CAP slots, the warp first copies them (column indices and values,
+// or permutation entries for a transposed tile set) into shared memory with
+// coalesced loads, then every lane walks its own tile there, so that gather k
+// of the 32 lanes reads entry k of 32 neighbouring tiles: where neighbouring
+// tiles touch neighbouring columns (banded and stencil matrices), one gather
+// instruction then touches one or two lines of the dense vector instead of up
+// to 32.  A warp whose tiles hold more atoms reads them straight from global
+// memory.  Each lane sums its tile's atoms in order, in chunks of 256 whose
+// partials are added in order (as the plain thread-mapped kernel does).
+template <int CAP>
+__global__ void __launch_bounds__(256) tm_staged_spmv_kernel(const int32_t* __restrict__ rp, int32_t num_tiles,
+                                                             AtomView at, float* __restrict__ out) {
+  constexpr int WPB = 8, CHUNK = 256;
+  __shared__ int s_idx[WPB][CAP];
+  __shared__ int s_val[WPB][CAP];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int32_t* vsrc = at.perm ? at.perm : reinterpret_cast<const int32_t*>(at.val);
+  const int64_t groups = ((int64_t)num_tiles + 31) / 32;
+  for (int64_t g = (int64_t)blockIdx.x * WPB + warp; g < groups; g += (int64_t)gridDim.x * WPB) {
+    const int64_t t = g * 32 + lane;
+    const int64_t t_last = min((int64_t)num_tiles, g * 32 + 32);
+    const int a0 = __ldg(rp + g * 32), a1 = __ldg(rp + t_last);
+    const int b = t < num_tiles ? __ldg(rp + t) : a1;
+    const int e = t < num_tiles ? __ldg(rp + t + 1) : a1;
+    float total = 0.f;
+    if (a1 - a0 <= CAP) {
+      for (int k = a0 + lane; k < a1; k += 32) {
+        s_idx[warp][k - a0] = ld_stream(at.idx + k);
+        s_val[warp][k - a0] = ld_stream(vsrc + k);
+      }
+      __syncwarp();
+      const int* si = s_idx[warp] - a0;
+      const int* sv = s_val[warp] - a0;
+      for (int k0 = b; k0 < e; k0 += CHUNK) {
+        const int k1 = min(e, k0 + CHUNK);
+        float part = 0.f;
+        int k = k0;
+        for (; k + 4 <= k1; k += 4) {
+          const float g0 = at.gather(si[k], 0), g1 = at.gather(si[k + 1], 0), g2 = at.gather(si[k + 2], 0),
+                      g3 = at.gather(si[k + 3], 0);
+          float w0, w1, w2, w3;
+          if (at.perm) {
+            w0 = __ldg(at.val + sv[k]);
+            w1 = __ldg(at.val + sv[k + 1]);
+            w2 = __ldg(at.val + sv[k + 2]);
+            w3 = __ldg(at.val + sv[k + 3]);
+          } else {
+            w0 = __int_as_float(sv[k]);
+            w1 = __int_as_float(sv[k + 1]);
+            w2 = __int_as_float(sv[k + 2]);
+            w3 = __int_as_float(sv[k + 3]);
+          }
+          part += w0 * g0;
+          part += w1 * g1;
+          part += w2 * g2;
+          part += w3 * g3;
+        }
+        for (; k < k1; ++k) part += (at.perm ? __ldg(at.val + sv[k]) : __int_as_float(sv[k])) * at.gather(si[k], 0);
+        total += part;
+      }
+      __syncwarp();  // the slots are free again
+    } else {
+      for (int k0 = b; k0 < e; k0 += CHUNK) {
+        const int k1 = min(e, k0 + CHUNK);
+        float part = 0.f;
+        for (int k = k0; k < k1; ++k) part += at.product(k, 0);
+        total += part;
+      }
+    }
+    if (t < num_tiles) out[t] = total;
+  }
+}
+
 // ----------------------------------------------------------- group-mapped --
 
 // Group-mapped schedule (Sec. 5.2.3), G threads per group, G a power of two

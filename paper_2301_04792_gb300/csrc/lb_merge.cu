@@ -732,6 +732,31 @@ lb_status_t launch_mp_expand(const MpTable& t, const SpmvCall& c, const float* d
   return LB_OK;
 }
 
+constexpr int kStagedCap = 864;  // atoms a warp's 32 tiles may hold to be staged in shared memory (27 x 32)
+
+// one wave of CTAs of the staged thread-mapped kernel (queried once per plan)
+int tm_staged_grid(int num_sms) {
+  int o = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, lbk::tm_staged_spmv_kernel<kStagedCap>, kBlock, 0) !=
+          cudaSuccess ||
+      o < 1)
+    o = 1;
+  return num_sms * o;
+}
+
+lb_status_t launch_tm_staged_spmv(const SpmvCall& c, int grid, cudaStream_t s) {
+  if (c.num_tiles == 0) return LB_OK;
+  // one warp per 32 tiles, grid-stride over the groups
+  const int64_t groups = ((int64_t)c.num_tiles + 31) / 32;
+  int64_t blocks = (groups + 7) / 8;
+  if (blocks > grid) blocks = grid;
+  if (blocks < 1) blocks = 1;
+  lbk::tm_staged_spmv_kernel<kStagedCap><<<(unsigned)blocks, kBlock, 0, s>>>(
+      c.rp, c.num_tiles, lbk::AtomView{c.idx, c.val, c.perm, c.vec, c.check, c.status}, c.out);
+  LB_CUDA_TRY(cudaGetLastError());
+  return LB_OK;
+}
+
 lb_status_t launch_tm_spmv(const SpmvCall& c, cudaStream_t s) {
   if (c.num_tiles == 0) return LB_OK;
   // Listing 3 launches ceil(rows / 256) blocks of 256 threads

@@ -86,7 +86,7 @@ class Plan:
     def __init__(self, tile_offsets: torch.Tensor, num_atoms: int | None = None, schedule="merge_path",
                  num_cols: int = 0, items_per_thread: int = 0, group_size: int = 0, ctas_per_sm: int = 0,
                  validate: bool = False, mp_variant: int = 0, units_per_cta: int = 0, tiles_per_share: int = 0,
-                 items_per_thread_t: int = 0, row_weight: int = 0, stream=None):
+                 items_per_thread_t: int = 0, row_weight: int = 0, staged: bool = False, stream=None):
         self._lib = _lib.load()
         _need(tile_offsets, torch.int32, "tile_offsets")
         self.tile_offsets = tile_offsets
@@ -100,7 +100,8 @@ class Plan:
         opts = PlanOpts(num_cols=int(num_cols), items_per_thread=int(items_per_thread), group_size=int(group_size),
                         ctas_per_sm=int(ctas_per_sm), validate=int(bool(validate)), mp_variant=int(mp_variant),
                         units_per_cta=int(units_per_cta), tiles_per_share=int(tiles_per_share),
-                        items_per_thread_t=int(items_per_thread_t), row_weight=int(row_weight))
+                        items_per_thread_t=int(items_per_thread_t), row_weight=int(row_weight),
+                        staged=int(bool(staged)))
         h = ctypes.c_void_p()
         check(self._lib.lb_plan_ex(ctypes.byref(h), _ptr(tile_offsets), self.num_tiles, self.num_atoms,
                                    int(Schedule.parse(schedule)), ctypes.byref(opts), ctypes.c_void_p(_stream(stream))),
@@ -229,6 +230,8 @@ class Plan:
 
 def _candidate_name(c) -> str:
     s = Schedule(c.schedule)
+    if s == Schedule.THREAD_MAPPED and c.staged:
+        return "thread_mapped_staged"
     if s == Schedule.MERGE_PATH:
         u = f"_u{c.units_per_cta}" if c.units_per_cta > 1 else ""
         w = f"_w{c.row_weight}" if c.row_weight > 1 else ""
@@ -267,11 +270,12 @@ def autotune(tile_offsets: torch.Tensor, col_idx: torch.Tensor, vals: torch.Tens
         cands.append({"name": _candidate_name(c), "schedule": Schedule(c.schedule).name.lower(),
                       "items_per_thread": c.items_per_thread, "group_size": c.group_size,
                       "mp_variant": c.mp_variant, "units_per_cta": c.units_per_cta, "row_weight": c.row_weight,
+                      "staged": c.staged,
                       "ms": c.ms, "gbps": c.gbps, "reps": c.reps, "status": c.status})
     report = {"candidates": cands, "best": cands[res.best]["name"],
               "heuristic": cands[res.heuristic]["name"] if res.heuristic >= 0 else None,
               "from_cache": bool(res.from_cache), "best_schedule": Schedule(res.best_schedule).name.lower(),
-              "best_opts": {f: getattr(res.best_opts, f) for f, _ in PlanOpts._fields_ if f != "reserved"},
+              "best_opts": {f: getattr(res.best_opts, f) for f, _ in PlanOpts._fields_},
               "y": y}
     return Plan._adopt(h, tile_offsets, N, C), report
 
@@ -508,10 +512,9 @@ def batch_autotune(rows, cols, nnz, rp_cat: torch.Tensor, col_cat: torch.Tensor,
         c = res.candidates[i]
         cands.append({"name": _batch_candidate_name(c.opts), "ms": c.ms, "gbps": c.gbps, "reps": c.reps,
                       "status": c.status,
-                      "opts": {f: getattr(c.opts, f) for f, _ in PlanOpts._fields_ if f != "reserved"}})
+                      "opts": {f: getattr(c.opts, f) for f, _ in PlanOpts._fields_}})
     report = {"candidates": cands, "best": cands[res.best]["name"], "from_cache": bool(res.from_cache),
-              "passes": passes, "best_opts": {f: getattr(res.best_opts, f) for f, _ in PlanOpts._fields_
-                                              if f != "reserved"},
+              "passes": passes, "best_opts": {f: getattr(res.best_opts, f) for f, _ in PlanOpts._fields_},
               "y": y_cat, "dx": dx_cat, "dvals": dvals_cat}
     return BatchPlan._adopt(h, rows, cols, nnz, rp_cat), report
 

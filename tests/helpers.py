@@ -7,7 +7,7 @@ import workloads as W
 TOL = oracle.TOL  # |y - y64| <= 1e-5 * sum |a_ij x_j|
 
 # every schedule and option set the library offers for one matrix (forward parity runs all of them)
-SCHEDULES = [("thread_mapped", {}), ("warp_mapped", {}), ("block_mapped", {}),
+SCHEDULES = [("thread_mapped", {}), ("thread_mapped", {"staged": True}), ("warp_mapped", {}), ("block_mapped", {}),
              ("group_mapped", {"group_size": 4}), ("group_mapped", {"group_size": 8}),
              ("group_mapped", {"group_size": 16}), ("group_mapped", {"group_size": 64}),
              ("group_mapped", {"group_size": 128}),

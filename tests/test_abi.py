@@ -48,7 +48,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_version_and_status_strings(lib):
-    assert lib.lb_version() >= 10000
+    assert lib.lb_version() >= 10100
     for s in range(7):
         assert lib.lb_status_string(s).decode().startswith(_lib.STATUS_NAMES[s])
 
@@ -106,7 +106,7 @@ def test_autotune_rejects_bad_args_before_any_launch(lib):
     assert b"num_cols" in lib.lb_last_error()
     assert plan.value is None
     assert ctypes.sizeof(_lib.PlanOpts) == 12 * 4
-    assert ctypes.sizeof(_lib.TuneResult) == 5 * 4 + ctypes.sizeof(_lib.PlanOpts) + 20 * 40
+    assert ctypes.sizeof(_lib.TuneResult) == 5 * 4 + ctypes.sizeof(_lib.PlanOpts) + 20 * 44
 
 
 def test_plan_rejects_row_weight_out_of_range_before_any_launch(lib):
@@ -126,7 +126,9 @@ def test_candidate_names_carry_units_and_row_weight():
     assert lbm._candidate_name(c) == "merge_path_ipt8_v0_u4"
     c = _lib.TuneCandidate(schedule=3, items_per_thread=8, mp_variant=3, units_per_cta=1, row_weight=0)
     assert lbm._candidate_name(c) == "merge_path_ipt8_v3"
-    assert ctypes.sizeof(_lib.TuneCandidate) == 10 * 4
+    c = _lib.TuneCandidate(schedule=0, staged=1)
+    assert lbm._candidate_name(c) == "thread_mapped_staged"
+    assert ctypes.sizeof(_lib.TuneCandidate) == 11 * 4
 
 
 def test_selftest_rejects_unknown_case_without_launching(lib):
@@ -140,7 +142,7 @@ def test_autotune_cache_file_round_trip(lib, tmp_path):
     saves back to the same text, reloads after a clear; lines of another
     library version or that do not parse are skipped."""
     ver = lib.lb_version()
-    cands = "[[3,8,0,0,1,1,0,5,0.5,1900.25],[3,4,0,0,1,2,0,5,0.25,3800.5],[0,0,0,0,1,1,0,1,12.5,7.75]]"
+    cands = "[[3,8,0,0,1,1,0,0,5,0.5,1900.25],[3,4,0,0,1,2,0,0,5,0.25,3800.5],[0,0,0,0,1,1,1,0,1,12.5,7.75]]"
     opts = ",".join(str(v) for v in (1000000, 4, 0, 0, 0, 0, 0, 1, 0, 0, 2, 0))
 
     def line(v, rows, fp):

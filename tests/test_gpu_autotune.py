@@ -27,8 +27,8 @@ def test_autotune_powerlaw_picks_fastest_and_matches_oracle(lbmod):
     plan, rep = lbmod.autotune(rp, ci, v, xd, num_cols=m.num_cols, reps=3, use_cache=False)
     cands = rep["candidates"]
     # merge-path warp x3 static + x2 row-weighted + x2 look-back, CTA x4 (buffers are aligned),
-    # thread-mapped, group-mapped x7
-    assert len(cands) == 19
+    # thread-mapped as printed and staged, group-mapped x7
+    assert len(cands) == 20
     assert all(c["status"] == 0 for c in cands), cands
     assert all(c["ms"] > 0 and c["reps"] in (1, 3) for c in cands)
     assert rep["heuristic"] == "merge_path_ipt8_v0" and cands[0]["name"] == "merge_path_ipt8_v0"

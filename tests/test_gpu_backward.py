@@ -9,7 +9,7 @@ from helpers import assert_within_bound, edge_cases, small_cases, to_dev
 
 pytestmark = pytest.mark.gpu
 
-BWD_SCHEDULES = [("thread_mapped", {}), ("warp_mapped", {}), ("block_mapped", {}),
+BWD_SCHEDULES = [("thread_mapped", {}), ("thread_mapped", {"staged": True}), ("warp_mapped", {}), ("block_mapped", {}),
                  ("group_mapped", {"group_size": 8}), ("merge_path", {"items_per_thread": 4}),
                  ("merge_path", {"items_per_thread": 8}), ("merge_path", {"items_per_thread": 16}),
                  ("merge_path", {"items_per_thread": 8, "mp_variant": 1}),

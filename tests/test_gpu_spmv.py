@@ -222,7 +222,8 @@ def test_full_powerlaw_1M(lbmod):
 
 
 def test_full_rmat_and_stencil(lbmod):
-    sched = [("thread_mapped", {}), ("warp_mapped", {}), ("block_mapped", {}), ("merge_path", {})]
+    sched = [("thread_mapped", {}), ("thread_mapped", {"staged": True}), ("warp_mapped", {}), ("block_mapped", {}),
+             ("merge_path", {}), ("merge_path", {"items_per_thread": 8, "mp_variant": 3})]
     m = W.rmat()
     full_size_check(lbmod, m, W.x_for(m), sched)
     del m
