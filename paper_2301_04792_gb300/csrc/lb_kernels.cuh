@@ -1612,22 +1612,36 @@ __global__ void __launch_bounds__(BLOCK) tm_spmv_kernel(const int32_t* __restric
 // thread-mapped loop; the staging is the shared-memory use of Sec. 5.2.3).
 // A warp takes 32 consecutive tiles, one per lane.  When their atoms fit in
 // the warp's CAP slots, the warp first copies them (column indices and values,
-// or permutation entries for a transposed tile set) into shared memory with
-// coalesced loads, then every lane walks its own tile there, so that gather k
-// of the 32 lanes reads entry k of 32 neighbouring tiles: where neighbouring
-// tiles touch neighbouring columns (banded and stencil matrices), one gather
+// or permutation entries for a transposed tile set) into shared memory --
+// 16-byte asynchronous copies (cp.async, no register round trip, all in
+// flight at once) when both arrays are 16-byte aligned, else coalesced plain
+// loads -- then every lane walks its own tile there, so that gather k of the
+// 32 lanes reads entry k of 32 neighbouring tiles: where neighbouring tiles
+// touch neighbouring columns (banded and stencil matrices), one gather
 // instruction then touches one or two lines of the dense vector instead of up
 // to 32.  A warp whose tiles hold more atoms reads them straight from global
 // memory.  Each lane sums its tile's atoms in order, in chunks of 256 whose
 // partials are added in order (as the plain thread-mapped kernel does).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 template <int CAP>
 __global__ void __launch_bounds__(256) tm_staged_spmv_kernel(const int32_t* __restrict__ rp, int32_t num_tiles,
                                                              AtomView at, float* __restrict__ out) {
   constexpr int WPB = 8, CHUNK = 256;
-  __shared__ int s_idx[WPB][CAP];
-  __shared__ int s_val[WPB][CAP];
+  static_assert(CAP % 4 == 0, "the last 16-byte copy must end inside the slot");
+  // CAP atoms plus up to 3 before the first one (copies start on a 16-byte boundary)
+  __shared__ __align__(16) int s_idx[WPB][CAP + 4];
+  __shared__ __align__(16) int s_val[WPB][CAP + 4];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int32_t* vsrc = at.perm ? at.perm : reinterpret_cast<const int32_t*>(at.val);
+  const bool async = ((reinterpret_cast<uintptr_t>(at.idx) | reinterpret_cast<uintptr_t>(vsrc)) & 15u) == 0;
+  const int num_atoms = __ldg(rp + num_tiles);
   const int64_t groups = ((int64_t)num_tiles + 31) / 32;
   for (int64_t g = (int64_t)blockIdx.x * WPB + warp; g < groups; g += (int64_t)gridDim.x * WPB) {
     const int64_t t = g * 32 + lane;
@@ -1637,13 +1651,27 @@ __global__ void __launch_bounds__(256) tm_staged_spmv_kernel(const int32_t* __re
     const int e = t < num_tiles ? __ldg(rp + t + 1) : a1;
     float total = 0.f;
     if (a1 - a0 <= CAP) {
-      for (int k = a0 + lane; k < a1; k += 32) {
-        s_idx[warp][k - a0] = ld_stream(at.idx + k);
-        s_val[warp][k - a0] = ld_stream(vsrc + k);
+      const int base = a0 & ~3;
+      if (async) {
+        // 16-byte chunks from the aligned start; a chunk at the end of the arrays copies only
+        // what exists (the rest of its slot is zero-filled)
+        const int nchunk = (a1 - base + 3) >> 2;
+        for (int c = lane; c < nchunk; c += 32) {
+          const int k = base + 4 * c;
+          const int bytes = 4 * min(4, num_atoms - k);
+          cp_async16(&s_idx[warp][4 * c], at.idx + k, bytes);
+          cp_async16(&s_val[warp][4 * c], vsrc + k, bytes);
+        }
+        cp_async_wait_all();
+      } else {
+        for (int k = a0 + lane; k < a1; k += 32) {
+          s_idx[warp][k - base] = ld_stream(at.idx + k);
+          s_val[warp][k - base] = ld_stream(vsrc + k);
+        }
       }
       __syncwarp();
-      const int* si = s_idx[warp] - a0;
-      const int* sv = s_val[warp] - a0;
+      const int* si = s_idx[warp] - base;
+      const int* sv = s_val[warp] - base;
       for (int k0 = b; k0 < e; k0 += CHUNK) {
         const int k1 = min(e, k0 + CHUNK);
         float part = 0.f;
