@@ -956,7 +956,7 @@ def run_ours(args, ws, rank, local):
 
 
 PROFILE_CASES = ("lookback_rmat", "lookback_stencil", "thread_mapped_powerlaw", "block_mapped_powerlaw", "spmm_k32_powerlaw",
-                 "sssp_rmat", "batch_fwd_bwd_diff4", "gather_probe_powerlaw")
+                 "sssp_rmat", "batch_fwd_bwd_diff4", "gather_probe_powerlaw", "staged_stencil")
 
 
 def run_case(name: str):
@@ -1008,7 +1008,8 @@ def run_case(name: str):
             bp.spmv(ci, v, x)
             bp.backward(ci, v, x, dy)
     else:
-        m = W.rmat() if name == "lookback_rmat" else W.stencil27() if name == "lookback_stencil" else W.powerlaw()
+        m = (W.rmat() if name == "lookback_rmat" else W.stencil27() if name in ("lookback_stencil", "staged_stencil")
+             else W.powerlaw())
         rp, ci, v = d(m.rp, m.ci, m.v)
         x = torch.rand(m.num_cols, device=dev)
         y = torch.empty(m.num_rows, device=dev)
@@ -1018,6 +1019,8 @@ def run_case(name: str):
             p = lb.Plan(rp, m.nnz, "merge_path", num_cols=m.num_cols, items_per_thread=8, mp_variant=3)
         elif name == "thread_mapped_powerlaw":
             p = lb.Plan(rp, m.nnz, "thread_mapped")
+        elif name == "staged_stencil":
+            p = lb.Plan(rp, m.nnz, "thread_mapped", staged=True)
         elif name == "block_mapped_powerlaw":
             p = lb.Plan(rp, m.nnz, "block_mapped")
         else:
