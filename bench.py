@@ -1000,9 +1000,10 @@ def run_case(name: str):
         b = W.diff_batch(num=4)
         rows, cols, nnz = b.rows(), b.cols(), b.nnz()
         rp_cat, ci, v = d(b.rp_cat(), b.ci_cat(), b.v_cat())
-        x = torch.rand(int(cols.sum()), device=dev)
-        dy = torch.rand(int(rows.sum()), device=dev)
-        bp = lb.BatchPlan(rows, cols, nnz, rp_cat, mp_variant=3, items_per_thread=4)
+        x, dy = d(np.concatenate([W.x_for(m, seed=i) for i, m in enumerate(b.mats)]),
+                  np.concatenate([W.dy_for(m, seed=i) for i, m in enumerate(b.mats)]))
+        # the configuration the batch autotuner picks for the 64-matrix workload
+        bp = lb.BatchPlan(rows, cols, nnz, rp_cat, mp_variant=3, items_per_thread=4, tiles_per_share=2)
         bp.prepare_backward(ci)
         for _ in range(3):
             bp.spmv(ci, v, x)

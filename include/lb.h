@@ -84,7 +84,7 @@ typedef struct lb_plan_opts_t {
                                IPT items in merge order (the per-thread form of Sec. 5.2.1); 2 = CTAs
                                with a bulk-copy (TMA) ring and the two-pass split (needs 16-byte aligned
                                buffers, else 1 is used); 3 = warps as in 0 on shares of guided sizes (about
-                               half of a warp's remaining part each, down to tiles_per_share tiles) taken in
+                               4/5 of a warp's remaining part each, down to tiles_per_share tiles) taken in
                                merge order from a counter, each share's carry resolved by a decoupled
                                look-back over the preceding shares' published partial sums (no block
                                barrier, no fix-up pass; bounded waits report LB_ERR_TIMEOUT) */

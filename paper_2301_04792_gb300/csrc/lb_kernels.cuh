@@ -1242,7 +1242,7 @@ __device__ __forceinline__ bool look_back(const unsigned long long* records, int
 // the carries resolved by a decoupled look-back (no block barrier, no fix-up
 // pass).  The plan cuts the rows + atoms into num_workers shares of whole warp
 // tiles in merge order, large first and down to tiles_per_share tiles at the
-// end (guided sizes: each share about half the remaining work of one warp),
+// end (guided sizes: each share about 4/5 of the remaining work of one warp),
 // so that the warps finish together.  A warp takes its next share from a
 // counter two tiles before the end of the current one, loads that share's
 // first tile while it reduces its last one, and walks tile after tile with
