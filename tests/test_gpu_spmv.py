@@ -148,8 +148,9 @@ def test_validation_reports_bad_inputs(lbmod):
     # out-of-range columns read as 0 and are reported by lb_status
     bad_ci = ci.clone()
     bad_ci[17] = 500
-    for s in ("thread_mapped", "warp_mapped", "merge_path"):
-        p = lbmod.Plan(rp, m.nnz, s, num_cols=500, validate=True)
+    for s, kw in (("thread_mapped", {}), ("thread_mapped", {"staged": True}), ("warp_mapped", {}),
+                  ("merge_path", {}), ("merge_path", {"mp_variant": 3})):
+        p = lbmod.Plan(rp, m.nnz, s, num_cols=500, validate=True, **kw)
         p.spmv(ci, v, x)
         p.status()  # clean
         p.spmv(bad_ci, v, x)
