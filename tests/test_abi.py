@@ -180,3 +180,26 @@ def test_batch_autotune_rejects_bad_arguments(lib):
     assert lib.lb_batch_autotune(*args, 1, ctypes.byref(opts), None, None, None) == 1
     assert lib.lb_batch_autotune(0, *args[1:], 1, ctypes.byref(opts), ctypes.byref(res), None, None) == 1
     assert lib.lb_batch_autotune(*args, 3, ctypes.byref(opts), ctypes.byref(res), None, None) == 1
+
+
+def test_batch_autotune_cache_lines_round_trip(lib, tmp_path):
+    """Batch autotuner entries share the cache file: a handwritten batch line loads beside a
+    single-matrix line and both save back to the same text."""
+    ver = lib.lb_version()
+    opts = ",".join(str(v) for v in (0, 4, 0, 0, 0, 3, 0, 0, 2, 0, 0, 0))
+    cand = "[%s,0,3,16.125,1928.5],[%s,0,3,17.75,1750.25]" % (opts, opts)
+    bline = ('{"format":"lb_batch_autotune_cache","version":%d,"device":"NVIDIA GB300/152/10.3","mats":64,'
+             '"rows":67108864,"cols":67108864,"atoms":1024724164,"fingerprint":"0x00000000000000ff","passes":7,'
+             '"cold_l2":0,"best":0,"best_opts":[%s],"candidates":[%s]}\n' % (ver, opts, cand))
+    sline = ('{"format":"lb_autotune_cache","version":%d,"device":"NVIDIA GB300/152/10.3","rows":10,"atoms":20,'
+             '"cols":10,"fingerprint":"0x0000000000000001","families":15,"cold_l2":0,"best":0,"heuristic":0,'
+             '"best_schedule":3,"best_opts":[%s],"candidates":[[3,8,0,0,1,1,0,0,5,0.5,1.5]]}\n' % (ver, opts))
+    src = tmp_path / "both.jsonl"
+    src.write_text(sline + bline + bline.replace('"best":0', '"best":5'))  # last: best out of range
+    lib.lb_autotune_cache_clear()
+    n = ctypes.c_int32(-1)
+    assert lib.lb_autotune_cache_load(str(src).encode(), ctypes.byref(n)) == 0 and n.value == 2
+    out = tmp_path / "saved.jsonl"
+    assert lib.lb_autotune_cache_save(str(out).encode()) == 0
+    assert sorted(out.read_text().splitlines(keepends=True)) == sorted([sline, bline])
+    lib.lb_autotune_cache_clear()
