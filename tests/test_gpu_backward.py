@@ -71,6 +71,36 @@ def test_backward_only_one_output(lbmod):
     assert_within_bound(dx.cpu().numpy(), dx64, bx, "dx only")
 
 
+def test_dvals_and_atom_tiles_on_unaligned_buffers(lbmod):
+    """The expand kernel loads column indices as 16-byte vectors and stores a vector lying wholly inside
+    a tile with one 16-byte store only when the buffers are 16-byte aligned: every mix of aligned and
+    offset buffers gives the same bits, and nothing is written outside the output."""
+    import torch
+    m = W.powerlaw(20_000, 20_000, 400_000, lmax=20_000, seed=4)
+    x, dy = W.x_for(m), W.dy_for(m)
+    _, _, dv32 = oracle.grad(m.rp, m.ci, m.v, x, dy, m.num_cols, want_dx=False)
+    rows = oracle.row_of_atom(m.rp)
+    rp, v, xd, dyd = to_dev(m.rp, m.v, x, dy)
+    ci_buf = torch.zeros(m.nnz + 1, dtype=torch.int32, device="cuda")
+    for opts in ({"items_per_thread": 4}, {"items_per_thread": 8}, {"items_per_thread": 4, "mp_variant": 3}):
+        plan = lbmod.Plan(rp, m.nnz, "merge_path", num_cols=m.num_cols, **opts)
+        for ci_off in (0, 1):
+            ci = ci_buf[ci_off:ci_off + m.nnz]
+            ci.copy_(torch.from_numpy(m.ci))
+            for out_off in (0, 1, 3):
+                dv_buf = torch.full((m.nnz + 4,), float("nan"), device="cuda")
+                dv = dv_buf[out_off:out_off + m.nnz]
+                plan.backward(m.num_cols, ci, v, xd, dyd, want_dx=False, dvals=dv)
+                assert np.array_equal(dv.cpu().numpy().view(np.uint32), dv32.view(np.uint32)), (opts, ci_off, out_off)
+                assert torch.isnan(dv_buf[:out_off]).all() and torch.isnan(dv_buf[out_off + m.nnz:]).all()
+        for out_off in (0, 1, 2):
+            t_buf = torch.full((m.nnz + 4,), -7, dtype=torch.int32, device="cuda")
+            t = t_buf[out_off:out_off + m.nnz]
+            plan.atom_tiles(out=t)
+            assert np.array_equal(t.cpu().numpy(), rows), (opts, out_off)
+            assert bool((t_buf[:out_off] == -7).all()) and bool((t_buf[out_off + m.nnz:] == -7).all())
+
+
 def test_autograd_function(lbmod):
     import torch
     m = W.powerlaw(4000, 3000, 60_000, lmax=3000, plant_long=False, seed=6)
