@@ -2,10 +2,11 @@
 // one more loop over the columns of B), on two of the paper's schedules:
 //  - merge-path: a warp per share of rows + atoms (the split table of Sec.
 //    5.2.1 with warp tiles), the lanes holding the columns of B; per tile the
-//    atoms and row ends are staged in shared memory, every row of the tile is
-//    summed over its atoms with four rows of B in flight, and the row left open
-//    at the share's end is finished by a second launch that adds the partial
-//    sums of each run of shares to the row that closes it, in share order;
+//    atoms and row ends are staged in shared memory and summed (with 16-byte
+//    rows of B, by lane groups over contiguous runs of the tile's atoms; else
+//    row by row with several rows of B in flight), and the row left open at
+//    the share's end is finished by a second launch that adds the partial sums
+//    of each run of shares to the row that closes it, in share order;
 //  - thread-mapped: Listing 4 as printed, one thread per row looping over the
 //    columns of B and the row's atoms.
 // Columns are processed in panels of up to 128 (four per lane).
@@ -171,11 +172,18 @@ __global__ void __launch_bounds__(256) spmm_mp_kernel(SpmmArgs a) {
   }
 }
 
-// The same walk with 16-byte rows of B: lane l holds columns 4 (l mod CL) ..
-// 4 (l mod CL) + 3 of the panel, so a row of B is CL float4 loads and the warp
-// takes G = 32 / CL atoms per instruction (group l / CL takes every G-th atom
-// of a row, four rounds in flight); at the row's end a fixed butterfly over
-// the groups adds their sums, leaving the same total in every group.  Needs
+// The same shares with 16-byte rows of B: lane l holds columns 4 (l mod CL) ..
+// 4 (l mod CL) + 3 of the panel, so a row of B is CL float4 loads, and the
+// warp's G = 32 / CL lane groups split each tile's atoms into G contiguous
+// runs, the way the SpMV warp walker splits them over its lanes: a group sums
+// its run in atom order with U rows of B in flight and closes a row at each
+// atom that ends one (marked in the row pass).  A row closed inside a group's
+// run is stored at once; the first row a group closes, and the row left open
+// at its run's end, are finished by a segmented scan over the groups in order
+// with the running carry in front (Hillis-Steele steps, a fixed tree).  Every
+// group keeps its gathers in flight whatever the rows' lengths, instead of one
+// row's gathers at a time (power-law 1M: K = 8 437 -> 249 us, K = 32 649 ->
+// 482 us, K = 128 unchanged at 1.54 ms, where B's rows come from HBM).  Needs
 // B, C 16-byte aligned, ldb, ldc and the panel width multiples of 4.
 template <int CL>
 __global__ void __launch_bounds__(256) spmm_mp_vec_kernel(SpmmArgs a) {
@@ -183,72 +191,111 @@ __global__ void __launch_bounds__(256) spmm_mp_vec_kernel(SpmmArgs a) {
   constexpr int G = 32 / CL;
   constexpr int U = 4;
   __shared__ int2 s_cv[WPB][kTileCap];
-  __shared__ int s_end[WPB][kTileCap];
+  __shared__ int s_mark[WPB][kTileCap];  // local row whose last atom this is, -1 if none
+  __shared__ int s_end[WPB][kTileCap];   // local end (exclusive) of each row of the tile
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane / CL, col = 4 * (lane % CL);
   const bool active = col < a.K;
   int2* cv_s = s_cv[warp];
+  int* mark_s = s_mark[warp];
   int* end_s = s_end[warp];
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  auto add4 = [](float4 x, float4 y) { return make_float4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w); };
+  auto shfl_up4 = [](float4 v, int d) {
+    return make_float4(__shfl_up_sync(lbk::kFull, v.x, d), __shfl_up_sync(lbk::kFull, v.y, d),
+                       __shfl_up_sync(lbk::kFull, v.z, d), __shfl_up_sync(lbk::kFull, v.w, d));
+  };
+  auto store4 = [&](int row, float4 v) {
+    if (active) *reinterpret_cast<float4*>(a.C + (int64_t)row * a.ldc + col) = v;
+  };
   const int nwarps = gridDim.x * WPB;
   for (int s = blockIdx.x * WPB + warp; s < a.num_shares; s += nwarps) {
     const int2* sp = a.splits + (size_t)s * (a.tpc + 1);
     int2 c0 = __ldg(sp);
     const int2 e1 = __ldg(sp + a.tpc);
     const int ntiles = (int)(((int64_t)(e1.x - c0.x) + (e1.y - c0.y) + a.items_per_tile - 1) / a.items_per_tile);
-    float4 carry = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 carry = zero;
     for (int k = 0; k < ntiles; ++k) {
       const int2 c1 = __ldg(sp + k + 1);
       const int nnz = c1.y - c0.y, nrows = c1.x - c0.x;
-      for (int i = lane; i < nnz; i += 32)
+      for (int i = lane; i < nnz; i += 32) {
         cv_s[i] = make_int2(lbk::ld_stream(a.idx + c0.y + i), __float_as_int(lbk::ld_stream(a.val + c0.y + i)));
+        mark_s[i] = -1;
+      }
       for (int i = lane; i < nrows; i += 32) end_s[i] = __ldg(a.rp + c0.x + 1 + i) - c0.y;
       __syncwarp();
-      int j = 0;
-      for (int r = 0; r <= nrows; ++r) {
-        const int e = r < nrows ? end_s[r] : nnz;
-        float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int q0 = j; q0 < e; q0 += U * G) {
-          float4 bq[U];
-          float w[U];
-#pragma unroll
-          for (int u = 0; u < U; ++u) {
-            const int q = q0 + u * G + g;
-            w[u] = 0.f;
-            bq[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (q < e) {
-              const int2 cv = cv_s[q];
-              w[u] = __int_as_float(cv.y);
-              if (active) bq[u] = __ldg(reinterpret_cast<const float4*>(a.B + (int64_t)cv.x * a.ldb + col));
-            }
-          }
-#pragma unroll
-          for (int u = 0; u < U; ++u) {
-            p.x += w[u] * bq[u].x;
-            p.y += w[u] * bq[u].y;
-            p.z += w[u] * bq[u].z;
-            p.w += w[u] * bq[u].w;
-          }
-        }
-#pragma unroll
-        for (int o = CL; o < 32; o <<= 1) {
-          p.x += __shfl_xor_sync(lbk::kFull, p.x, o);
-          p.y += __shfl_xor_sync(lbk::kFull, p.y, o);
-          p.z += __shfl_xor_sync(lbk::kFull, p.z, o);
-          p.w += __shfl_xor_sync(lbk::kFull, p.w, o);
-        }
-        if (r == 0) {  // the row open at the tile's start: the earlier tiles' partial sum in front
-          p.x = carry.x + p.x;
-          p.y = carry.y + p.y;
-          p.z = carry.z + p.z;
-          p.w = carry.w + p.w;
-        }
-        if (r < nrows) {
-          if (g == 0 && active) *reinterpret_cast<float4*>(a.C + (int64_t)(c0.x + r) * a.ldc + col) = p;
-        } else {
-          carry = p;
-        }
-        j = e;
+      // row pass: a row with atoms in the tile marks its last one; a row with none gets 0, or
+      // the carry if it is the tile's first row (it closes where the tile starts)
+      for (int r = lane; r < nrows; r += 32) {
+        const int e = end_s[r], pe = r > 0 ? end_s[r - 1] : 0;
+        if (e > pe) mark_s[e - 1] = r;
       }
+      for (int r = g; r < nrows; r += G) {
+        const int e = end_s[r], pe = r > 0 ? end_s[r - 1] : 0;
+        if (e == pe) store4(c0.x + r, r == 0 ? carry : zero);
+      }
+      __syncwarp();
+      // this group's run of atoms
+      const int per = (nnz + G - 1) / G;
+      const int qa = g * per, qb = min(nnz, qa + per);
+      float4 acc = zero, head = zero;
+      int first = -1;
+      for (int q0 = qa; q0 < qb; q0 += U) {
+        float4 bq[U];
+        float w[U];
+        int mk[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int q = q0 + u;
+          w[u] = 0.f;
+          mk[u] = -1;
+          bq[u] = zero;
+          if (q < qb) {
+            const int2 cv = cv_s[q];
+            w[u] = __int_as_float(cv.y);
+            mk[u] = mark_s[q];
+            if (active) bq[u] = __ldg(reinterpret_cast<const float4*>(a.B + (int64_t)cv.x * a.ldb + col));
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          acc.x += w[u] * bq[u].x;
+          acc.y += w[u] * bq[u].y;
+          acc.z += w[u] * bq[u].z;
+          acc.w += w[u] * bq[u].w;
+          if (mk[u] >= 0) {
+            if (first < 0) {
+              head = acc;
+              first = mk[u];
+            } else {
+              store4(c0.x + mk[u], acc);
+            }
+            acc = zero;
+          }
+        }
+      }
+      // segmented scan over the groups: the partial sum of the row open at each group's end
+      // (reset where a group closed a row), then the carry in front of the groups before the
+      // first reset -- unless the tile's first row closed where the tile starts and took it
+      const float4 cin = nrows > 0 && end_s[0] == 0 ? zero : carry;
+      float4 v = acc;
+      int f = first >= 0;
+#pragma unroll
+      for (int o = 1; o < G; o <<= 1) {
+        const float4 vo = shfl_up4(v, o * CL);
+        const int fo = __shfl_up_sync(lbk::kFull, f, o * CL);
+        if (g >= o) {
+          if (!f) v = add4(vo, v);
+          f |= fo;
+        }
+      }
+      if (!f) v = add4(cin, v);
+      float4 in = shfl_up4(v, CL);
+      if (g == 0) in = cin;
+      if (first >= 0) store4(c0.x + first, add4(in, head));
+      const int src = (G - 1) * CL + (lane % CL);
+      carry = make_float4(__shfl_sync(lbk::kFull, v.x, src), __shfl_sync(lbk::kFull, v.y, src),
+                          __shfl_sync(lbk::kFull, v.z, src), __shfl_sync(lbk::kFull, v.w, src));
       __syncwarp();
       c0 = c1;
     }

@@ -70,6 +70,15 @@ def test_spmm_powerlaw(lbmod):
     check(lbmod, m, 32, "merge_path", reps=3)
 
 
+def test_spmm_shares_of_several_tiles(lbmod):
+    """Enough rows + atoms that every warp share spans several tiles, so the partial sum of a row open
+    at a tile's end crosses into the next tile of the same share, including tiles that start at a row's
+    end marker (the row closes where the tile starts)."""
+    m = W.powerlaw(600_000, 400_000, 12_000_000, lmax=60_000, seed=21)
+    for K in (8, 32, 12, 7):  # 16-byte rows of B (K = 12: a partly idle lane group) and scalar ones
+        check(lbmod, m, K, "merge_path", seed=K)
+
+
 def test_spmm_unsupported_and_bad_arguments(lbmod):
     import torch
     from paper_2301_04792_gb300 import _lib
