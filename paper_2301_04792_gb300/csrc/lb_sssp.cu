@@ -5,12 +5,12 @@
 // with stride G, finding each edge's vertex with get_tile (a binary search in
 // the prefix, Sec. 5.2.3).  Each edge relaxes its head with an atomic minimum
 // on the distance's bits (non-negative floats order like their bit patterns),
-// and a head whose distance dropped joins the next frontier once (a per-vertex
-// flag, double-buffered by iteration parity so that clearing the current
-// flags never races with setting the next ones).  The host loops until the
-// frontier is empty.  The distances are the least fixed point of
-// dist[v] = min over edges (u, v) of fl32(dist[u] + w), whatever order the
-// relaxations take, so they are deterministic.
+// issued without waiting for its result, four edges per thread at a time.  A
+// pass over the vertices then puts every vertex whose distance dropped in this
+// iteration on the next frontier (its distance at the previous pass is kept
+// beside it).  The host loops until the frontier is empty.  The distances are
+// the least fixed point of dist[v] = min over edges (u, v) of fl32(dist[u] +
+// w), whatever order the relaxations take, so they are deterministic.
 #include <algorithm>
 #include <cmath>
 #include <string>
@@ -32,9 +32,13 @@ __global__ void sssp_check_edges_kernel(const int32_t* __restrict__ col, const f
   }
 }
 
-__global__ void sssp_init_kernel(int* __restrict__ dist_bits, int32_t V, int32_t source, int32_t* front) {
-  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x)
-    dist_bits[v] = v == source ? 0 : 0x7f800000;  // +0, +inf
+__global__ void sssp_init_kernel(int* __restrict__ dist_bits, int* __restrict__ prev_bits, int32_t V,
+                                 int32_t source, int32_t* front) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
+    const int d = v == source ? 0 : 0x7f800000;  // +0, +inf
+    dist_bits[v] = d;
+    prev_bits[v] = d;
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) front[0] = source;
 }
 
@@ -42,12 +46,11 @@ template <int BLOCK, int G>
 __global__ void __launch_bounds__(BLOCK) sssp_relax_kernel(const int32_t* __restrict__ rp,
                                                            const int32_t* __restrict__ col,
                                                            const float* __restrict__ w, int* dist_bits,
-                                                           const int32_t* __restrict__ front, int32_t nfront,
-                                                           int* flag_cur, int* flag_next, int32_t* next,
-                                                           int32_t* next_count) {
+                                                           const int32_t* __restrict__ front, int32_t nfront) {
   constexpr int GPB = BLOCK / G;             // groups per block
   constexpr int WPG = G >= 32 ? G / 32 : 1;  // warps per group
   constexpr int SW = G < 32 ? G : 32;        // shuffle width
+  constexpr int R = 4;                       // edges per thread in flight
   __shared__ int s_pre[GPB][G + 1];
   __shared__ int s_base[GPB][G];
   __shared__ float s_dist[GPB][G];
@@ -56,7 +59,6 @@ __global__ void __launch_bounds__(BLOCK) sssp_relax_kernel(const int32_t* __rest
   const int lane = threadIdx.x % G;
   const int sl = threadIdx.x % SW;
   const int wg = lane / 32;
-  const int wl = threadIdx.x & 31;
 
   auto group_sync = [&]() {
     if constexpr (G <= 32) {
@@ -79,7 +81,6 @@ __global__ void __launch_bounds__(BLOCK) sssp_relax_kernel(const int32_t* __rest
       s_base[g][lane] = b;
       // a relaxed read: a distance lowered meanwhile puts u back on the next frontier
       s_dist[g][lane] = __int_as_float(__ldcg(dist_bits + u));
-      flag_cur[u] = 0;  // nobody sets the current flags in this iteration
     }
     int wtotal;
     int ex = lbk::group_excl_scan_small<SW>(len, sl, wtotal);
@@ -94,43 +95,70 @@ __global__ void __launch_bounds__(BLOCK) sssp_relax_kernel(const int32_t* __rest
     if (lane == G - 1) s_pre[g][G] = ex + len;
     group_sync();
     const int total = s_pre[g][G];
-    int rounds_total = total;
-    if constexpr (G < 32) rounds_total = __reduce_max_sync(lbk::kFull, total);
-    for (int a0 = 0; a0 < rounds_total; a0 += G) {
-      const int aa = a0 + lane;
-      bool push = false;
-      int head = 0;
-      if (aa < total) {
-        int lo = 0, hi = G - 1;  // get_tile: the largest tile whose prefix is <= aa
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (s_pre[g][mid] <= aa) lo = mid;
-          else hi = mid - 1;
+    for (int a0 = lane; a0 < total; a0 += R * G) {
+      int k[R], lo[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int aa = a0 + r * G;
+        k[r] = -1;
+        lo[r] = 0;
+        if (aa < total) {
+          int l = 0, hi = G - 1;  // get_tile: the largest tile whose prefix is <= aa
+          while (l < hi) {
+            const int mid = (l + hi + 1) >> 1;
+            if (s_pre[g][mid] <= aa) l = mid;
+            else hi = mid - 1;
+          }
+          lo[r] = l;
+          k[r] = s_base[g][l] + (aa - s_pre[g][l]);
         }
-        const int k = s_base[g][lo] + (aa - s_pre[g][lo]);
-        head = __ldg(col + k);
-        const float nd = s_dist[g][lo] + __ldg(w + k);
-        const int old = atomicMin(dist_bits + head, __float_as_int(nd));
-        if (nd < __int_as_float(old)) push = atomicExch(flag_next + head, 1) == 0;
       }
-      // one counter update per warp for the heads that join the next frontier
-      const unsigned m = __ballot_sync(lbk::kFull, push);
-      if (m) {
-        int base = 0;
-        const int leader = __ffs(m) - 1;
-        if (wl == leader) base = atomicAdd(next_count, __popc(m));
-        base = __shfl_sync(lbk::kFull, base, leader);
-        if (push) next[base + __popc(m & ((1u << wl) - 1u))] = head;
+      int head[R];
+      float wt[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        head[r] = k[r] >= 0 ? __ldg(col + k[r]) : 0;
+        wt[r] = k[r] >= 0 ? __ldg(w + k[r]) : 0.f;
       }
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (k[r] >= 0) atomicMin(dist_bits + head[r], __float_as_int(s_dist[g][lo[r]] + wt[r]));
     }
     group_sync();
   }
 }
 
+// The next frontier: every vertex whose distance dropped since the last pass,
+// appended with one counter update per warp; its distance at this pass is kept.
+__global__ void sssp_frontier_kernel(const int* __restrict__ dist_bits, int* __restrict__ prev_bits, int32_t V,
+                                     int32_t* next, int32_t* next_count) {
+  const int wl = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v0 = blockIdx.x * (int64_t)blockDim.x; v0 < V; v0 += stride) {
+    const int64_t v = v0 + threadIdx.x;
+    bool push = false;
+    if (v < V) {
+      const int d = __ldcg(dist_bits + v);
+      if (d < prev_bits[v]) {
+        prev_bits[v] = d;
+        push = true;
+      }
+    }
+    const unsigned m = __ballot_sync(lbk::kFull, push);
+    if (m) {
+      int base = 0;
+      const int leader = __ffs(m) - 1;
+      if (wl == leader) base = atomicAdd(next_count, __popc(m));
+      base = __shfl_sync(lbk::kFull, base, leader);
+      if (push) next[base + __popc(m & ((1u << wl) - 1u))] = (int32_t)v;
+    }
+  }
+}
+
 template <int G>
 void relax_launch(int64_t blocks, const int32_t* rp, const int32_t* col, const float* w, int* dist_bits,
-                  const int32_t* front, int32_t n, int* fc, int* fn, int32_t* next, int32_t* cnt, cudaStream_t s) {
-  sssp_relax_kernel<kBlock, G><<<(unsigned)blocks, kBlock, 0, s>>>(rp, col, w, dist_bits, front, n, fc, fn, next, cnt);
+                  const int32_t* front, int32_t n, cudaStream_t s) {
+  sssp_relax_kernel<kBlock, G><<<(unsigned)blocks, kBlock, 0, s>>>(rp, col, w, dist_bits, front, n);
 }
 
 }  // namespace
@@ -157,18 +185,18 @@ lb_status_t lb_sssp(const int32_t* tile_offsets, int32_t num_vertices, int32_t n
   int dev = 0;
   LB_CUDA_TRY(cudaGetDevice(&dev));
   const int sms = device_sms(dev);
-  // scratch: two flag arrays, two frontier lists, the next-frontier count and the weight check
+  // scratch: the distances at the last frontier pass, two frontier lists, the next-frontier count and
+  // the weight check
   void* buf = nullptr;
   const size_t vbytes = sizeof(int) * (size_t)V;
-  LB_CUDA_TRY(cudaMalloc(&buf, 4 * vbytes + 256));
+  LB_CUDA_TRY(cudaMalloc(&buf, 3 * vbytes + 256));
   struct Free {
     void* p;
     ~Free() { cudaFree(p); }
   } guard{buf};
-  int* flags[2] = {static_cast<int*>(buf), static_cast<int*>(buf) + V};
-  int32_t* lists[2] = {static_cast<int32_t*>(buf) + 2 * (size_t)V, static_cast<int32_t*>(buf) + 3 * (size_t)V};
-  int32_t* counters = reinterpret_cast<int32_t*>(static_cast<char*>(buf) + 4 * vbytes);  // [0] next count, [1] bad
-  LB_CUDA_TRY(cudaMemsetAsync(buf, 0, 2 * vbytes, s));
+  int* prev_bits = static_cast<int*>(buf);
+  int32_t* lists[2] = {static_cast<int32_t*>(buf) + (size_t)V, static_cast<int32_t*>(buf) + 2 * (size_t)V};
+  int32_t* counters = reinterpret_cast<int32_t*>(static_cast<char*>(buf) + 3 * vbytes);  // [0] next count, [1] bad
   LB_CUDA_TRY(cudaMemsetAsync(counters, 0, 256, s));
   if (num_edges > 0) {
     const unsigned wb = (unsigned)std::min<int64_t>(((int64_t)num_edges + 255) / 256, (int64_t)sms * 32);
@@ -177,7 +205,7 @@ lb_status_t lb_sssp(const int32_t* tile_offsets, int32_t num_vertices, int32_t n
   }
   int* dist_bits = reinterpret_cast<int*>(dist);
   const unsigned ib = (unsigned)std::min<int64_t>(((int64_t)V + 255) / 256, (int64_t)sms * 32);
-  sssp_init_kernel<<<ib, 256, 0, s>>>(dist_bits, V, source, lists[0]);
+  sssp_init_kernel<<<ib, 256, 0, s>>>(dist_bits, prev_bits, V, source, lists[0]);
   LB_CUDA_TRY(cudaGetLastError());
   int bad = 0;
   LB_CUDA_TRY(cudaMemcpyAsync(&bad, counters + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -200,14 +228,16 @@ lb_status_t lb_sssp(const int32_t* tile_offsets, int32_t num_vertices, int32_t n
     blocks = std::min<int64_t>(blocks, (int64_t)sms * 64);
     const int nx = 1 - cur;
     switch (G) {
-      case 4: relax_launch<4>(blocks, tile_offsets, col_idx, weights, dist_bits, lists[cur], n, flags[cur], flags[nx], lists[nx], counters, s); break;
-      case 8: relax_launch<8>(blocks, tile_offsets, col_idx, weights, dist_bits, lists[cur], n, flags[cur], flags[nx], lists[nx], counters, s); break;
-      case 16: relax_launch<16>(blocks, tile_offsets, col_idx, weights, dist_bits, lists[cur], n, flags[cur], flags[nx], lists[nx], counters, s); break;
-      case 32: relax_launch<32>(blocks, tile_offsets, col_idx, weights, dist_bits, lists[cur], n, flags[cur], flags[nx], lists[nx], counters, s); break;
-      case 64: relax_launch<64>(blocks, tile_offsets, col_idx, weights, dist_bits, lists[cur], n, flags[cur], flags[nx], lists[nx], counters, s); break;
-      case 128: relax_launch<128>(blocks, tile_offsets, col_idx, weights, dist_bits, lists[cur], n, flags[cur], flags[nx], lists[nx], counters, s); break;
-      default: relax_launch<256>(blocks, tile_offsets, col_idx, weights, dist_bits, lists[cur], n, flags[cur], flags[nx], lists[nx], counters, s); break;
+      case 4: relax_launch<4>(blocks, tile_offsets, col_idx, weights, dist_bits, lists[cur], n, s); break;
+      case 8: relax_launch<8>(blocks, tile_offsets, col_idx, weights, dist_bits, lists[cur], n, s); break;
+      case 16: relax_launch<16>(blocks, tile_offsets, col_idx, weights, dist_bits, lists[cur], n, s); break;
+      case 32: relax_launch<32>(blocks, tile_offsets, col_idx, weights, dist_bits, lists[cur], n, s); break;
+      case 64: relax_launch<64>(blocks, tile_offsets, col_idx, weights, dist_bits, lists[cur], n, s); break;
+      case 128: relax_launch<128>(blocks, tile_offsets, col_idx, weights, dist_bits, lists[cur], n, s); break;
+      default: relax_launch<256>(blocks, tile_offsets, col_idx, weights, dist_bits, lists[cur], n, s); break;
     }
+    LB_CUDA_TRY(cudaGetLastError());
+    sssp_frontier_kernel<<<ib, 256, 0, s>>>(dist_bits, prev_bits, V, lists[nx], counters);
     LB_CUDA_TRY(cudaGetLastError());
     LB_CUDA_TRY(cudaMemcpyAsync(&n, counters, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     LB_CUDA_TRY(cudaStreamSynchronize(s));
