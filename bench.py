@@ -818,6 +818,18 @@ def run_ours(args, ws, rank, local):
         t_plan.append(time.perf_counter() - t0)
         p_.close()
     plan_ms = statistics.median(t_plan) * 1e3
+    # the backward's set-up (the transpose: a stable counting sort of the atoms by column, and the
+    # transposed tile set's plan), once per sparsity pattern and cached in the plan
+    t_tr = []
+    for _ in range(1 if args.ncu else 3):
+        p_ = lb.Plan(rp_d[0], N, "merge_path", num_cols=C, items_per_thread=args.ipt, row_weight=args.row_weight)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p_.prepare_backward(C, ci_d[0])
+        torch.cuda.synchronize()
+        t_tr.append(time.perf_counter() - t0)
+        p_.close()
+    prep_ms = statistics.median(t_tr) * 1e3
 
     # zero copy: the kernel streams col_idx / vals straight from pinned host memory over the
     # host link (x copied in, y copied out); the same plan, nothing staged in HBM
@@ -944,6 +956,10 @@ def run_ours(args, ws, rank, local):
                     "plan_note": "lb_plan (split table built on the device; allocates, synchronises) runs once per "
                                  "sparsity pattern and is not in ms_per_step: every step reuses the plan"},
             "e2e_zero_copy": zc,
+            "prepare_backward": {"ms": round(prep_ms, 3), "GBps_at_16B_per_nnz": round(16 * N / (prep_ms * 1e-3) / 1e9, 2),
+                                 "note": "host wall clock of lb_prepare_backward on the same matrix: the transpose "
+                                         "(histogram, scan, stable radix sort of (column, atom) pairs, row gather) "
+                                         "and the transposed tile set's plan; once per sparsity pattern"},
             "gpu_launches": args.steps * info["kernels_per_spmv"],
             "clocks": clocks,
             "batched": batched,

@@ -100,51 +100,81 @@ __global__ void radix_upsweep_kernel(const int32_t* __restrict__ keys, int64_t n
   hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = s_cnt[threadIdx.x];
 }
 
-// Stable scatter of one tile.  Atoms are visited in index order: round r holds
-// atoms base + r*256 + [0, 256), warp w its 32 lanes.  An atom's position is the
-// tile's base for its digit + atoms of that digit in earlier rounds + in earlier
-// warps of this round + in earlier lanes of its warp.
-__global__ void radix_downsweep_kernel(const int32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in,
-                                       int64_t n, int shift, const int32_t* __restrict__ hist_scan, int64_t ntiles,
-                                       int32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out) {
-  __shared__ int s_base[256];
-  __shared__ int s_run[256];
-  __shared__ int s_wc[kRadixWarps][256];
+// Stable scatter of one tile.  Warp w owns the tile's atoms w*512 + [0, 512),
+// visited in 16 rounds of 32 consecutive atoms (so atom order is warp, round,
+// lane order).  A first walk counts each warp's atoms per digit (peers from
+// __match_any_sync, counts kept by the warp in shared memory, no block
+// barrier); the counts give every (warp, digit) its offset inside the digit's
+// run of the tile and every digit its start in the tile.  A second walk over
+// the same atoms (keys kept in registers, values read now) ranks them again
+// and places each at its slot of the tile, ordered by digit, in shared
+// memory; the tile is then written out run by run, each digit's run to its
+// global start, so the stores of neighbouring threads land on neighbouring
+// addresses.
+__global__ void __launch_bounds__(kRadixBlock, 4) radix_downsweep_kernel(
+    const int32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in, int64_t n, int shift,
+    const int32_t* __restrict__ hist_scan, int64_t ntiles, int32_t* __restrict__ keys_out,
+    int32_t* __restrict__ vals_out) {
+  constexpr int kPerWarp = 32 * kRadixItems;
+  __shared__ int s_base[256];             // global start of each digit's run of this tile
+  __shared__ int s_loc[256];              // start of each digit's run inside the tile
+  __shared__ int s_cnt[kRadixWarps][256];  // a warp's atoms per digit, then its offset in the run
+  __shared__ int s_w[kRadixWarps];
+  __shared__ int2 s_kv[kRadixTile];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  s_base[tid] = hist_scan[(int64_t)tid * ntiles + blockIdx.x];
-  s_run[tid] = 0;
   const unsigned lt = (1u << lane) - 1u;
-  const int64_t base = (int64_t)blockIdx.x * kRadixTile;
-  for (int r = 0; r < kRadixItems; ++r) {
+  s_base[tid] = hist_scan[(int64_t)tid * ntiles + blockIdx.x];
 #pragma unroll
-    for (int w = 0; w < kRadixWarps; ++w) s_wc[w][tid] = 0;
-    __syncthreads();
-    const int64_t i = base + (int64_t)r * kRadixBlock + tid;
+  for (int w = 0; w < kRadixWarps; ++w) s_cnt[w][tid] = 0;
+  __syncthreads();
+  const int64_t tbase = (int64_t)blockIdx.x * kRadixTile;
+  const int64_t wbase = tbase + (int64_t)warp * kPerWarp;
+  int key[kRadixItems];
+#pragma unroll
+  for (int r = 0; r < kRadixItems; ++r) {
+    const int64_t i = wbase + r * 32 + lane;
     const bool valid = i < n;
-    const int key = valid ? keys_in[i] : 0;
-    const int val = valid ? (vals_in ? vals_in[i] : (int)i) : 0;
-    const int d = valid ? ((key >> shift) & 255) : 256;
+    key[r] = valid ? keys_in[i] : 0;
+    const int d = valid ? ((key[r] >> shift) & 255) : 256;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    if (valid && __popc(peers & lt) == 0) s_cnt[warp][d] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // thread tid = digit: offsets of the warps inside the digit's run, and the run's start in the tile
+  int tot = 0;
+#pragma unroll
+  for (int w = 0; w < kRadixWarps; ++w) {
+    const int c = s_cnt[w][tid];
+    s_cnt[w][tid] = tot;
+    tot += c;
+  }
+  s_loc[tid] = block_incl_scan_int(tot, s_w) - tot;
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kRadixItems; ++r) {
+    const int64_t i = wbase + r * 32 + lane;
+    const bool valid = i < n;
+    const int d = valid ? ((key[r] >> shift) & 255) : 256;
     const unsigned peers = __match_any_sync(0xffffffffu, d);
     const int rank = __popc(peers & lt);
-    if (valid && rank == 0) s_wc[warp][d] = __popc(peers);
-    __syncthreads();
-    {
-      int run = s_run[tid];
-#pragma unroll
-      for (int w = 0; w < kRadixWarps; ++w) {
-        const int c = s_wc[w][tid];
-        s_wc[w][tid] = run;
-        run += c;
-      }
-      s_run[tid] = run;
-    }
-    __syncthreads();
+    const int off = valid ? s_cnt[warp][d] : 0;
+    __syncwarp();
     if (valid) {
-      const int pos = s_base[d] + s_wc[warp][d] + rank;
-      keys_out[pos] = key;
-      vals_out[pos] = val;
+      s_kv[s_loc[d] + off + rank] = make_int2(key[r], vals_in ? vals_in[i] : (int)i);
+      if (rank == 0) s_cnt[warp][d] = off + __popc(peers);
     }
-    __syncthreads();
+    __syncwarp();
+  }
+  __syncthreads();
+  const int64_t left = n - tbase;
+  const int count = left < kRadixTile ? (int)left : kRadixTile;
+  for (int p = tid; p < count; p += kRadixBlock) {
+    const int2 kv = s_kv[p];
+    const int d = (kv.x >> shift) & 255;
+    const int pos = s_base[d] + (p - s_loc[d]);
+    keys_out[pos] = kv.x;
+    vals_out[pos] = kv.y;
   }
 }
 
