@@ -203,72 +203,89 @@ struct DevBuf {
 
 }  // namespace
 
-lb_status_t device_scan(const int32_t* in, int32_t* out, int64_t n, bool inclusive, cudaStream_t s) {
-  if (n <= 0) return LB_OK;
+namespace {
+
+// entries of scratch a scan of n items needs: the tile totals of every level above the first
+int64_t scan_scratch(int64_t n) {
+  int64_t t = 0;
+  while (n > kScanTile) {
+    n = (n + kScanTile - 1) / kScanTile;
+    t += n;
+  }
+  return t;
+}
+
+// scan of n items with the tile totals in caller scratch (scan_scratch(n) entries): launches only
+void scan_into(const int32_t* in, int32_t* out, int64_t n, bool inclusive, int32_t* scratch, cudaStream_t s) {
+  if (n <= 0) return;
   const int64_t tiles = (n + kScanTile - 1) / kScanTile;
   if (tiles == 1) {
     scan_apply_kernel<<<1, kScanBlock, 0, s>>>(in, out, n, nullptr, inclusive ? 1 : 0);
-    LB_CUDA_TRY(cudaGetLastError());
-    return LB_OK;
+    return;
   }
+  scan_reduce_kernel<<<(unsigned)tiles, kScanBlock, 0, s>>>(in, n, scratch);
+  scan_into(scratch, scratch, tiles, false, scratch + tiles, s);
+  scan_apply_kernel<<<(unsigned)tiles, kScanBlock, 0, s>>>(in, out, n, scratch, inclusive ? 1 : 0);
+}
+
+}  // namespace
+
+lb_status_t device_scan(const int32_t* in, int32_t* out, int64_t n, bool inclusive, cudaStream_t s) {
+  if (n <= 0) return LB_OK;
+  const int64_t need = scan_scratch(n);
   DevBuf sums;
-  LB_CUDA_TRY(cudaMalloc(&sums.p, sizeof(int32_t) * (size_t)tiles));
-  int32_t* ps = static_cast<int32_t*>(sums.p);
-  scan_reduce_kernel<<<(unsigned)tiles, kScanBlock, 0, s>>>(in, n, ps);
-  LB_CUDA_TRY(cudaGetLastError());
-  LB_TRY(device_scan(ps, ps, tiles, false, s));
-  scan_apply_kernel<<<(unsigned)tiles, kScanBlock, 0, s>>>(in, out, n, ps, inclusive ? 1 : 0);
+  if (need > 0) LB_CUDA_TRY(cudaMalloc(&sums.p, sizeof(int32_t) * (size_t)need));
+  scan_into(in, out, n, inclusive, static_cast<int32_t*>(sums.p), s);
   LB_CUDA_TRY(cudaGetLastError());
   // `sums` is freed when this returns; make sure the kernels using it are done
-  LB_CUDA_TRY(cudaStreamSynchronize(s));
+  if (need > 0) LB_CUDA_TRY(cudaStreamSynchronize(s));
   return LB_OK;
 }
 
+// One device allocation holds the sort's key and value buffers, its digit histograms and the scans'
+// tile totals; nothing synchronises until the sort is done.
 lb_status_t transpose_sort(const int32_t* keys, const int32_t* row_of, int64_t N, int32_t C, int32_t* cp,
                            int32_t* riT, int32_t* perm, cudaStream_t s) {
-  // cp: histogram of keys into cp[1..C], then inclusive scan
   LB_CUDA_TRY(cudaMemsetAsync(cp, 0, sizeof(int32_t) * ((size_t)C + 1), s));
   if (N == 0) return LB_OK;
-  histogram_kernel<<<grid_for(N, 256), 256, 0, s>>>(keys, N, cp + 1);
-  LB_CUDA_TRY(cudaGetLastError());
-  LB_TRY(device_scan(cp + 1, cp + 1, C, true, s));
-
   int bits = 0;
   while (bits < 31 && ((int64_t)1 << bits) < (int64_t)C) ++bits;
   const int passes = (bits + 7) / 8;
+  const int64_t ntiles = (N + kRadixTile - 1) / kRadixTile;
+  const int64_t nhist = passes > 0 ? 256 * ntiles : 0;
+  const int64_t nscan = std::max(scan_scratch(C), scan_scratch(nhist));
+  const int64_t nsort = passes > 0 ? 4 * N : 0;
+  DevBuf buf;
+  LB_CUDA_TRY(cudaMalloc(&buf.p, sizeof(int32_t) * (size_t)std::max<int64_t>(1, nsort + nhist + nscan)));
+  int32_t* base = static_cast<int32_t*>(buf.p);
+  int32_t* kbuf[2] = {base, base + N};
+  int32_t* vbuf[2] = {base + 2 * N, base + 3 * N};
+  int32_t* hist = base + nsort;
+  int32_t* scratch = hist + nhist;
+  // cp: histogram of keys into cp[1..C], then inclusive scan
+  histogram_kernel<<<grid_for(N, 256), 256, 0, s>>>(keys, N, cp + 1);
+  scan_into(cp + 1, cp + 1, C, true, scratch, s);
+  LB_CUDA_TRY(cudaGetLastError());
   if (passes == 0) {
     iota_kernel<<<grid_for(N, 256), 256, 0, s>>>(perm, N);
-    LB_CUDA_TRY(cudaGetLastError());
   } else {
-    const int64_t ntiles = (N + kRadixTile - 1) / kRadixTile;
-    DevBuf ka, kb, va, vb, hist;
-    LB_CUDA_TRY(cudaMalloc(&ka.p, sizeof(int32_t) * (size_t)N));
-    LB_CUDA_TRY(cudaMalloc(&kb.p, sizeof(int32_t) * (size_t)N));
-    LB_CUDA_TRY(cudaMalloc(&va.p, sizeof(int32_t) * (size_t)N));
-    LB_CUDA_TRY(cudaMalloc(&vb.p, sizeof(int32_t) * (size_t)N));
-    LB_CUDA_TRY(cudaMalloc(&hist.p, sizeof(int32_t) * (size_t)(256 * ntiles)));
     const int32_t* kin = keys;
     const int32_t* vin = nullptr;  // first pass: values are the atom indices
-    int32_t* kbuf[2] = {static_cast<int32_t*>(ka.p), static_cast<int32_t*>(kb.p)};
-    int32_t* vbuf[2] = {static_cast<int32_t*>(va.p), static_cast<int32_t*>(vb.p)};
     for (int p = 0; p < passes; ++p) {
       const int shift = 8 * p;
       int32_t* kout = kbuf[p & 1];
       int32_t* vout = (p == passes - 1) ? perm : vbuf[p & 1];
-      radix_upsweep_kernel<<<(unsigned)ntiles, kRadixBlock, 0, s>>>(kin, N, shift, static_cast<int32_t*>(hist.p),
-                                                                    ntiles);
-      LB_CUDA_TRY(cudaGetLastError());
-      LB_TRY(device_scan(static_cast<int32_t*>(hist.p), static_cast<int32_t*>(hist.p), 256 * ntiles, false, s));
-      radix_downsweep_kernel<<<(unsigned)ntiles, kRadixBlock, 0, s>>>(
-          kin, vin, N, shift, static_cast<int32_t*>(hist.p), ntiles, kout, vout);
-      LB_CUDA_TRY(cudaGetLastError());
+      radix_upsweep_kernel<<<(unsigned)ntiles, kRadixBlock, 0, s>>>(kin, N, shift, hist, ntiles);
+      scan_into(hist, hist, nhist, false, scratch, s);
+      radix_downsweep_kernel<<<(unsigned)ntiles, kRadixBlock, 0, s>>>(kin, vin, N, shift, hist, ntiles, kout, vout);
       kin = kout;
       vin = vout;
     }
-    LB_CUDA_TRY(cudaStreamSynchronize(s));
   }
+  LB_CUDA_TRY(cudaGetLastError());
   gather_kernel<<<grid_for(N, 256), 256, 0, s>>>(row_of, perm, N, riT);
   LB_CUDA_TRY(cudaGetLastError());
+  // `buf` is freed when this returns
   LB_CUDA_TRY(cudaStreamSynchronize(s));
   return LB_OK;
 }
