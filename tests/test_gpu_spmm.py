@@ -48,7 +48,7 @@ def check(lb, m, K, schedule, seed=0, pad_b=0, pad_c=0, reps=2, **kw):
         assert torch.equal(c2.view(torch.int32), outs[0][0].view(torch.int32)), "SpMM not bit-identical"
 
 
-@pytest.mark.parametrize("K", [1, 7, 8, 16, 32, 33, 64, 100, 128, 130, 256])
+@pytest.mark.parametrize("K", [1, 4, 7, 8, 16, 20, 32, 33, 64, 100, 128, 130, 256])
 def test_spmm_small_cases(lbmod, K):
     for name, m in small_cases() + edge_cases():
         check(lbmod, m, K, "merge_path")
